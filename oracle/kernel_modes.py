@@ -1,0 +1,322 @@
+"""Oracle: theta-Fourier modes of the S and K kernels for near pairs.
+
+TEST INFRASTRUCTURE ONLY.  Plain FP64 numpy, vectorised over a batch of
+pairs.  A pair is (target point r(t, th), source curve t_s); its output is
+the Fourier modes K_m, m = -M..M (M = Mth/2), of the kernel as a function
+of the source angle th_s:
+
+  S:  e^{ik rho}/rho                               (Section 3.2, Eq. (Sphi:appr2))
+  K:  alpha tau_1 - tau_3 - i beta tau_0           (Section 4, Eq. (dis:K))
+
+``method_modes`` follows the paper's algorithm step by step:
+  1. rho^2 on the Mth-point theta grid (Eq. (rho)); near samples use the
+     cancellation-free line integral of the Section 4 Remark.
+  2. a0 = real minimiser of rho^2, b0 = sqrt(2 rho^2(a0) / rho^2''(a0)),
+     then complex Newton for the root theta_+ = a + i b (Section 3.3).
+  3. F = (s_{a,b}/rho^2)^{1/2} (Lemma "singular1", Eq. (F-smooth)); modes.
+  4. A_m(b) (Eq. (Am), special.a_modes); singular convolution
+     <rho^{-1}>_l = sum_j <F>_j e^{-i(l-j)a} A_{|l-j|}  (Eq. (convolution)).
+  5. S: <cos(k rho)> (x) <rho^{-1}> + i <sin(k rho)/rho>   (Eq. (Sphi:appr2)).
+     K: <alpha> (x) (<tau_0> (x) <rho^{-1}>)  (Eqs. (dis:K), (tau1))
+        - <tau_3> (Eq. (tau3-standard) for b >= 0.01, Eq. (tau3-modified)
+        otherwise) - i <beta tau_0>.
+Every smooth factor keeps all Mth of its grid modes (the paper's p and M_0
+set to M), with the Nyquist mode split evenly between +M and -M.
+Convolutions are written as direct sums.
+
+``definition_modes`` is the plain definition <f>_m = (1/2pi) int f e^{-im th}
+evaluated by the trapezoid rule on a grid refined until it converges
+(brute force, no singularity swapping).
+"""
+import math
+import numpy as np
+
+from . import geometry as geo
+from . import special as sp
+
+STABLE_DELTA = 0.25     # |t - t_s| + |th - th_s| below which differences use the line integral
+ROOT_TOL = 1e-14        # Newton stops when |dzeta| <= ROOT_TOL*b + 4e-16|zeta| (then one more step)
+SERIES_X = 0.5          # alpha(rho), beta(rho) use their Taylor series when k rho < SERIES_X
+SMALL_B = 0.1           # translated swapping for tau_3 when b < SMALL_B (the paper uses 0.01)
+NEAR_PHI = 0.05         # |th_q - a| below which the translated remainder uses the stable sum
+B_CAP = 4.0             # roots farther than this from the real axis are replaced by (a0, B_CAP)
+
+
+# ----------------------------------------------------------------------------
+# small helpers
+# ----------------------------------------------------------------------------
+def sym_modes(v, M):
+    """Grid modes j = -M..M of samples v[..., 2M] (Nyquist split evenly)."""
+    c = np.fft.fft(v, axis=-1) / (2 * M)
+    out = np.zeros(v.shape[:-1] + (2 * M + 1,), complex)
+    out[..., M:2 * M] = c[..., 0:M]
+    out[..., 1:M] = c[..., M + 1:2 * M]
+    out[..., 0] = c[..., M] / 2
+    out[..., 2 * M] = c[..., M] / 2
+    return out
+
+
+def swap_convolution(f, a, A, lmax):
+    """sum_j f_j e^{-i(l-j)a} A_{|l-j|} for l = -lmax..lmax  (Eq. (convolution))."""
+    M = (f.shape[-1] - 1) // 2
+    j = np.arange(-M, M + 1)
+    l = np.arange(-lmax, lmax + 1)
+    d = l[:, None] - j[None, :]
+    kern = A[:, np.abs(d)] * np.exp(-1j * d[None, :, :] * a[:, None, None])
+    return np.einsum("bj,blj->bl", f, kern)
+
+
+def linear_convolution(u, v, vmax, wmax):
+    """w_m = sum_n u_n v_{m-n}, m = -wmax..wmax; u over -U..U, v over -vmax..vmax."""
+    U = (u.shape[-1] - 1) // 2
+    n = np.arange(-U, U + 1)
+    m = np.arange(-wmax, wmax + 1)
+    idx = m[:, None] - n[None, :]
+    assert np.all(np.abs(idx) <= vmax)
+    return np.einsum("bn,bmn->bm", u, v[:, idx + vmax])
+
+
+def _series_coeffs():
+    a = [(-1) ** (n + 1) * (1 - 2 * n) / math.factorial(2 * n) for n in range(1, 10)]
+    b = [(-1) ** (n + 1) * (2 * n) / math.factorial(2 * n + 1) for n in range(1, 10)]
+    return a, b
+
+
+_ALPHA_C, _BETA_C = _series_coeffs()
+
+
+def alpha_beta(rho, k):
+    """alpha = (1 - cos k rho - k rho sin k rho)/rho^2, beta = (sin k rho - k rho cos k rho)/rho^3."""
+    x = k * rho
+    alpha = (1 - np.cos(x) - x * np.sin(x)) / rho ** 2
+    beta = (np.sin(x) - x * np.cos(x)) / rho ** 3
+    small = x < SERIES_X
+    if np.any(small):
+        xs2 = x[small] ** 2
+        sa = sum(c * xs2 ** i for i, c in enumerate(_ALPHA_C))
+        sb = sum(c * xs2 ** i for i, c in enumerate(_BETA_C))
+        alpha[small] = k * k * sa
+        beta[small] = k ** 3 * sb
+    return alpha, beta
+
+
+def _near_mask(t_s, th_s, t, th):
+    return np.abs(t_s - t) + np.abs(np.real(geo.wrap_angle(th_s - th))) <= STABLE_DELTA
+
+
+# ----------------------------------------------------------------------------
+# complex root of rho^2 (Section 3.3)
+# ----------------------------------------------------------------------------
+def locate_root(surface, t, th, t_s, thq, rho2):
+    """a0, b0 and the Newton root (a, b) of rho^2(zeta) nearest to the real axis."""
+    B, Mt = rho2.shape
+    h = 2 * np.pi / Mt
+    q = np.argmin(rho2, axis=1)
+    a0 = thq[q].copy()
+    start = a0.copy()
+
+    def deriv(z):
+        near = _near_mask(t_s, z, t, th)
+        Y = geo.difference(surface, t_s, z, t, th, near)
+        _, _, rth, _, _, rthth = geo.evaluate(surface, t_s, z)
+        g0 = np.sum(Y * Y, -1)
+        g1 = 2 * np.sum(Y * rth, -1)
+        g2 = 2 * (np.sum(rth * rth, -1) + np.sum(Y * rthth, -1))
+        return g0, g1, g2
+
+    for _ in range(40):
+        g0, g1, g2 = deriv(a0)
+        step = np.where(g2 > 0, g1 / np.where(g2 > 0, g2, 1.0), 0.0)
+        step = np.clip(step, -h, h)
+        a0 = np.clip(a0 - step, start - h, start + h)
+        if np.all(np.abs(step) <= 1e-15 * (1 + np.abs(a0))):
+            break
+    g0, g1, g2 = deriv(a0)
+    b0 = np.sqrt(2 * g0 / np.where(g2 > 0, g2, 0.0))
+    capped = ~(b0 <= B_CAP)
+    zeta = a0 + 1j * np.where(capped, B_CAP, b0)
+    done = capped.copy()
+    extra = np.zeros(B, bool)
+    for _ in range(60):
+        g0, g1, _ = deriv(zeta)
+        dz = g0 / g1
+        upd = ~done
+        zn = zeta - dz
+        zn = np.where(zn.imag < 0, np.conj(zn), zn)
+        over = upd & ~(zn.imag <= B_CAP)
+        capped = capped | over
+        zn = np.where(over, a0 + 1j * B_CAP, zn)
+        zeta = np.where(upd, zn, zeta)
+        small = np.abs(dz) <= ROOT_TOL * np.abs(zeta.imag) + 4e-16 * np.abs(zeta)
+        done = done | over | (extra & upd)
+        extra = extra | small
+        if np.all(done):
+            break
+    return a0, b0, zeta.real, zeta.imag, done
+
+
+# ----------------------------------------------------------------------------
+# the method (singularity swapping)
+# ----------------------------------------------------------------------------
+def _pair_samples(surface, t, th, t_s, Mt):
+    thq = 2 * np.pi * np.arange(Mt) / Mt
+    T_s = np.broadcast_to(t_s[:, None], (len(t), Mt))
+    TH_s = np.broadcast_to(thq[None, :], (len(t), Mt))
+    T = np.broadcast_to(t[:, None], (len(t), Mt))
+    TH = np.broadcast_to(th[:, None], (len(t), Mt))
+    near = _near_mask(T_s, TH_s, T, TH)
+    Y = geo.difference(surface, T_s, TH_s, T, TH, near)
+    return thq, T_s, TH_s, T, TH, near, Y
+
+
+def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=False):
+    """Kernel modes by singularity swapping; dict kernel -> (B, Mt+1) complex (m = -M..M)."""
+    t = np.atleast_1d(np.asarray(t, float))
+    th = np.atleast_1d(np.asarray(th, float))
+    t_s = np.atleast_1d(np.asarray(t_s, float))
+    M = Mt // 2
+    thq, T_s, TH_s, T, TH, near, Y = _pair_samples(surface, t, th, t_s, Mt)
+    rho2 = np.sum(Y * Y, -1)
+    rho = np.sqrt(rho2)
+    a0, b0, a, b, ok = locate_root(surface, t, th, t_s, thq, rho2)
+    q = np.exp(-b)
+    phi = thq[None, :] - a[:, None]
+    s = (-np.expm1(-b))[:, None] ** 2 + 4 * q[:, None] * np.sin(phi / 2) ** 2   # Eq. (sab)
+    F = np.sqrt(s / rho2)                                                     # Eq. (F-smooth)
+    f = sym_modes(F, M)
+    need_k = "K" in kernels
+    L = (4 if need_k else 3) * M
+    A, D = sp.a_modes(b, L)
+    out = {}
+    rmax = 3 * M if need_k else 2 * M
+    R = swap_convolution(f, a, A, rmax)                                        # <rho^{-1}>_l
+    if "S" in kernels:
+        C = sym_modes(np.cos(k * rho), M)
+        Sn = sym_modes(np.sin(k * rho) / rho, M)
+        out["S"] = linear_convolution(C, R, rmax, M) + 1j * Sn
+    if need_k:
+        nu, _ = geo.normal_and_jacobian(surface, T_s, TH_s)
+        tau0 = np.sum(nu * Y, -1)
+        if np.any(near):
+            tau0[near] = geo.tau0_stable(surface, T_s[near], TH_s[near], T[near], TH[near])
+        alpha, beta = alpha_beta(rho, k)
+        T0 = sym_modes(tau0, M)
+        T1 = linear_convolution(T0, R, rmax, 2 * M)                            # Eq. (tau1)
+        AT1 = linear_convolution(sym_modes(alpha, M), T1, 2 * M, M)
+        T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s))
+        out["K"] = AT1 - T3 - 1j * sym_modes(beta * tau0, M)
+    if return_details:
+        out["_a"], out["_b"], out["_a0"], out["_b0"], out["_ok"] = a, b, a0, b0, ok
+        out["_R"], out["_rmax"] = R, rmax
+    return out
+
+
+def tau3_modes(H3, a, b, A, D, M, pair):
+    """<tau_3>_n, n = -M..M, from H3 = tau_0 F^3 (Eqs. (tau3-standard), (tau3-modified))."""
+    Bn = sp.b_modes(b, A[:, :2 * M + 2], D[:, :2 * M + 2])                  # B_m(0,b), m = 0..2M+1
+    h3 = sym_modes(H3, M)
+    out = swap_convolution(h3, a, Bn, M)                                       # standard form
+    small = b < SMALL_B
+    if np.any(small):
+        i = np.nonzero(small)[0]
+        surface, t, th, t_s = pair
+        Ha, H1a = h3_at_root(surface, t[i], th[i], t_s[i], a[i], b[i])
+        out[i] = _tau3_translated(H3[i], h3[i], a[i], b[i], A[i], Bn[i], M, Ha, H1a)
+    return out
+
+
+def h3_at_root(surface, t, th, t_s, a, b):
+    """H3(a) = tau_0(a) F(a)^3 and H3'(a), evaluated directly from the geometry at th_s = a.
+
+    s_{a,b}(a) = (1 - e^{-b})^2 and s'(a) = 0, so F(a) = (1 - e^{-b}) / rho(a) and
+    F'(a) = -F(a) (rho^2)'(a) / (2 rho^2(a)); tau_0'(a) = nu'(a) . (r_s(a) - r).
+    """
+    near = _near_mask(t_s, a, t, th)
+    Y = geo.difference(surface, t_s, a, t, th, near)
+    _, rt, rth, _, rtth, rthth = geo.evaluate(surface, t_s, a)
+    n = np.cross(rt, rth)
+    J = np.sqrt(np.sum(n * n, -1))
+    nu = n / J[:, None]
+    dn = np.cross(rtth, rth) + np.cross(rt, rthth)
+    dnu = (dn - nu * np.sum(nu * dn, -1)[:, None]) / J[:, None]
+    tau0 = np.sum(nu * Y, -1)
+    if np.any(near):
+        tau0[near] = geo.tau0_stable(surface, t_s[near], a[near], t[near], th[near])
+    rho2 = np.sum(Y * Y, -1)
+    F = -np.expm1(-b) / np.sqrt(rho2)
+    dF = -F * np.sum(Y * rth, -1) / rho2
+    dtau0 = np.sum(dnu * Y, -1)
+    return tau0 * F ** 3, dtau0 * F ** 3 + 3 * tau0 * F ** 2 * dF
+
+
+def _tau3_translated(H3, h3, a, b, A, Bn, M, H_a, H1_a):
+    """Translated singularity swapping for small b (Section 4, Eq. (tau3-modified))."""
+    Mt = 2 * M
+    kk = np.arange(-M, M + 1)
+    e = np.exp(1j * kk[None, :] * a[:, None])
+    thq = 2 * np.pi * np.arange(Mt) / Mt
+    phi = geo.wrap_angle(thq[None, :] - a[:, None])
+    close = np.abs(phi) < NEAR_PHI
+    den = np.where(close, 1.0, np.sin(phi / 2) ** 2)
+    Rs = (H3 - H_a[:, None] - H1_a[:, None] * np.sin(phi)) / den
+    for bi, qi in zip(*np.nonzero(close)):
+        p = phi[bi, qi]
+        s2 = np.sin(p / 2) ** 2
+        if s2 == 0.0:            # the limit 2 H3''(a)
+            Rs[bi, qi] = np.real(np.sum(-2 * kk * kk * h3[bi] * e[bi]))
+            continue
+        acc = 0.0
+        for kv, hv in zip(kk, h3[bi] * e[bi]):
+            kabs = abs(kv)
+            re = -2 * np.sin(kabs * p / 2) ** 2 / s2 if kabs else 0.0
+            # sin(k p) - k sin(p) = -2 sin(p) sum_{j<k} sin^2((k-1-2j) p/2)
+            ssum = sum(np.sin((kabs - 1 - 2 * j) * p / 2) ** 2 for j in range(kabs))
+            im = np.sign(kv) * (-2 * np.sin(p) * ssum) / s2
+            acc = acc + hv * (re + 1j * im)
+        Rs[bi, qi] = np.real(acc)
+    d = sym_modes(Rs, M)
+    q = np.exp(-b)
+    om2 = np.expm1(-b) ** 2
+    Lb = Bn.shape[1] - 1
+    m = np.arange(-Lb, Lb + 1)
+    Bfull = Bn[:, np.abs(m)] * np.exp(-1j * m[None, :] * a[:, None])        # B_m(a, b)
+    Btil = (A[:, :Lb + 1] - om2[:, None] * Bn) / (4 * q[:, None])            # B~_m(0, b), m = 0..Lb
+    n = np.arange(-M, M + 1)
+    c = Lb
+    out = H_a[:, None] * Bfull[:, n + c]
+    out = out + (H1_a / 2j)[:, None] * (np.exp(-1j * a)[:, None] * Bfull[:, n - 1 + c]
+                                        - np.exp(1j * a)[:, None] * Bfull[:, n + 1 + c])
+    out = out + swap_convolution(d, a, Btil, M)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the plain definition (brute force)
+# ----------------------------------------------------------------------------
+def definition_modes(surface, t, th, t_s, M, k, kernel="S", n_start=None, tol=1e-15, n_max=2 ** 22):
+    """<f>_m, m = -M..M, by the trapezoid rule refined until converged."""
+    n = n_start or max(8 * M, 64)
+    prev = None
+    while True:
+        thq = 2 * np.pi * np.arange(n) / n
+        near = _near_mask(t_s, thq, t, th)
+        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        rho = np.sqrt(np.sum(Y * Y, -1))
+        if kernel == "S":
+            f = np.exp(1j * k * rho) / rho
+        else:
+            nu, _ = geo.normal_and_jacobian(surface, np.full(n, t_s), thq)
+            tau0 = np.sum(nu * Y, -1)
+            if np.any(near):
+                tau0[near] = geo.tau0_stable(surface, np.full(near.sum(), t_s), thq[near],
+                                             np.full(near.sum(), t), np.full(near.sum(), th))
+            f = tau0 * np.exp(1j * k * rho) * (1j * k * rho - 1) / rho ** 3
+        c = np.fft.fft(f) / n
+        m = np.arange(-M, M + 1)
+        cur = c[m % n]
+        if prev is not None and np.max(np.abs(cur - prev)) <= tol * np.max(np.abs(cur)):
+            return cur, n
+        if n >= n_max:
+            return cur, n
+        prev = cur
+        n *= 2
