@@ -1,0 +1,194 @@
+/*
+ * bie.h -- C ABI of the B300 library for the FFT-accelerated surface boundary
+ * integral equation method for 3D Helmholtz scattering (singularity swapping
+ * for the theta-Fourier coefficients of the single- and double-layer kernels,
+ * panel-based generalized Gaussian quadrature, dense solve, field evaluation).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers are interleaved double pairs (re, im) ("double2").
+ *  - Every array argument marked [dev] is a CUDA device pointer owned by the
+ *    caller; [host] pointers are host memory owned by the caller.  The library
+ *    never frees caller memory.  Opaque handles (bie_ctx, bie_surface,
+ *    bie_matrix) are owned by the library and released by their *_free call.
+ *  - All GPU work is enqueued on the stream given to bie_ctx_create and is
+ *    asynchronous unless stated otherwise; results are visible after a stream
+ *    synchronisation.
+ *  - Errors are reported by the return value (bie_status); bie_last_error()
+ *    returns a thread-local description of the last failure.  No entry point
+ *    aborts, traps or falls back to the CPU: there is no CPU path.
+ *  - Index of an unknown / collocation node: (panel*16 + node)*Mth + l, with
+ *    panel = 0..Np-1 (uniform panels of [0, L]), node = 0..15 (Gauss-Legendre),
+ *    l = 0..Mth-1 (theta_l = 2 pi l / Mth).  The unknown is the weighted
+ *    density phi~ = phi J (Section 3, Eq. (S:para)).
+ */
+#ifndef BIE_H
+#define BIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BIE_OK = 0,
+  BIE_EINVAL = 1,        /* invalid argument (null pointer, size out of range) */
+  BIE_ENOMEM = 2,        /* device allocation failed */
+  BIE_ECUDA = 3,         /* a CUDA call failed; see bie_last_error() */
+  BIE_ENOCONV = 4,       /* the solver did not reach the tolerance within maxit */
+  BIE_ENAN = 5,          /* NaN/Inf detected in inputs or iterates */
+  BIE_ETIMEOUT = 6,      /* a bounded device wait expired */
+  BIE_EUNSUPPORTED = 7   /* valid request that this build does not implement */
+} bie_status;
+
+typedef struct bie_ctx_s* bie_ctx;
+typedef struct bie_surface_s* bie_surface;
+typedef struct bie_matrix_s* bie_matrix;
+
+/* ---- kernels and operators ------------------------------------------------ */
+#define BIE_KERNEL_S 1u  /* e^{ik rho}/rho                      (Section 3, Eq. (Sphi:appr2)) */
+#define BIE_KERNEL_K 2u  /* alpha tau1 - tau3 - i beta tau0      (Section 4, Eq. (dis:K))      */
+
+typedef enum {
+  BIE_OP_S = 0,          /* S                      (Eq. (bie:S))                          */
+  BIE_OP_K = 1,          /* K                                                             */
+  BIE_OP_K_PLUS_I = 2,   /* K + I  exterior Dirichlet, double layer (Eq. (bie:Kie))        */
+  BIE_OP_K_MINUS_I = 3,  /* K - I  interior Dirichlet, double layer (Eq. (bie:Kie))        */
+  BIE_OP_CFIE = 4        /* I + K - i eta S: exterior Dirichlet, combined field           */
+} bie_operator;
+
+/* ---- context ----------------------------------------------------------------
+ * bie_ctx_create: bind a context to the current CUDA device and to cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the handle.
+ * Errors: BIE_EINVAL (out == NULL), BIE_ECUDA.                                */
+bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream);
+void bie_ctx_free(bie_ctx ctx);
+const char* bie_last_error(void);
+/* Wait for all work of the context's stream; returns BIE_ECUDA on a device error. */
+bie_status bie_ctx_sync(bie_ctx ctx);
+
+/* ---- surfaces (Section 2, Eq. (para); Section 3.1) -------------------------
+ * kind 0, ellipsoid:  r = (a sin t cos th, b sin t sin th, c cos t), t in [0, pi]
+ * kind 1, star:       r = h(t,th) (sin t cos th, sin t sin th, cos t),
+ *                     h = 1 + sum_i c_i sin^p_i t cos^q_i t T_i(m_i th),
+ *                     T = cos (s_i = 0) or sin (s_i = 1); terms[5*i..5*i+4] =
+ *                     (c, p, q, m, s) as doubles, n_terms <= BIE_MAX_TERMS.   */
+#define BIE_MAX_TERMS 96
+typedef struct {
+  int kind;
+  int n_terms;
+  double axes[3];
+  const double* terms;   /* [host] 5*n_terms doubles, ignored for kind 0 */
+} bie_surface_desc;
+
+/* 16-node generalized Gaussian rules on the reference panel [-1, 1]
+ * (Section 3.1: self and adjacent panels, nodes and weights depend on the
+ * target node l).  x[d][l][g], w[d][l][g], d = delta + 1 with delta = -1
+ * (source panel left of the target panel), 0 (self), +1 (right).            */
+typedef struct {
+  double x[3][16][16];
+  double w[3][16][16];
+} bie_quad_tables;
+
+/* bie_surface_sample: sample the surface on the collocation grid (Np panels x
+ * 16 Legendre nodes x Mth angles) and on every GGQ source ring (one ring per
+ * target node, near panel and GGQ node, Mth angles each): positions, unit
+ * normals, Jacobians and the data the pair pipeline needs (Section 2 and the
+ * Section 4 Remark on second derivatives).  Allocates device memory owned by
+ * the returned handle.  Np in [2, 4096]; Mth even, in [8, 1024], of the form
+ * 2^a 3^b.  Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.                      */
+bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int n_panels,
+                              int m_theta, const bie_quad_tables* ggq, bie_surface* out);
+void bie_surface_free(bie_surface s);
+/* Number of unknowns N = 16*Np*Mth, and number of near pairs
+ * 256*Mth*(3Np-2) (targets x GGQ source nodes on the self and adjacent panels). */
+int64_t bie_surface_unknowns(bie_surface s);
+int64_t bie_surface_near_pairs(bie_surface s);
+/* [dev] views owned by the surface: node positions [N][3], unit normals [N][3],
+ * Jacobians [N] (double). */
+const double* bie_surface_points(bie_surface s);
+const double* bie_surface_normals(bie_surface s);
+const double* bie_surface_jacobians(bie_surface s);
+
+/* ---- kernel modes (Sections 3.2-3.3, 4) -----------------------------------
+ * For each pair p = (target row, source) with target row = flat node index
+ * (t_j^l, theta_i) and source = d*16 + g (the GGQ node g of the near panel
+ * j + d - 1), write the theta_s-Fourier modes K_m, m = -M..M (M = Mth/2), of
+ * each requested kernel (bit mask of BIE_KERNEL_*), computed by singularity
+ * swapping: complex root of rho^2 by Newton, smooth factor F = (s_{a,b}/rho^2)^{1/2}
+ * (Lemma "singular1"), A_m(b) by the difference recurrence or Miller's
+ * recurrence (Eqs. (Am), (diff-recurrence)), zero-padded FFT convolution
+ * (Eq. (convolution)), tau_3 by Eqs. (tau3-standard)/(tau3-modified).
+ *   pair_row  [dev] int64[n_pairs], pair_src [dev] int32[n_pairs]
+ *   modes_out [dev] double2[n_pairs][n_kernels][Mth+1], kernels in bit order
+ *   k > 0 wavenumber.
+ * Errors: BIE_EINVAL (bad sizes/pointers; a pair whose source panel does not
+ * exist yields zeros and BIE_EINVAL after the next bie_ctx_sync), BIE_ECUDA.   */
+bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                            const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
+                            double* modes_out);
+
+/* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------
+ * Fill the dense N x N matrix of operator op acting on the weighted density:
+ * preparation stage (Gauss-Legendre x trapezoid for every block) and
+ * correction stage (near blocks |i-j| <= 1 from the pair pipeline, Parseval
+ * weights, GGQ weights and Lagrange interpolation to the 16 Legendre nodes).
+ *   A_out [dev] double2[N][N] row-major (row = target), overwritten.
+ *   eta   coupling of BIE_OP_CFIE (ignored otherwise).
+ * Errors: BIE_EINVAL, BIE_ECUDA.                                              */
+bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta, double* A_out);
+
+/* Correction stage only: write the near-block entries of S (and/or K) into
+ * A_out (rows = targets), adding them to what is there.  The timed hot path. */
+bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                             double weight_s, double weight_k, double* A_out);
+
+/* ---- dense solve -------------------------------------------------------------
+ * Restarted FGMRES (right preconditioned, modified Gram-Schmidt with
+ * re-orthogonalisation) on A x = b for nrhs right-hand sides, one after the
+ * other, until ||b - A x|| <= tol ||b||.
+ *   A    [dev] double2[N][N] row-major;  rhs [dev] double2[nrhs][N];
+ *   x    [dev] double2[nrhs][N] (initial guess in, solution out).
+ *   prec 0 = FP64 matvec, 1 = FP32-stored matrix inside FGMRES with FP64
+ *        iterative refinement (outer residuals in FP64).
+ *   precond 0 = none, 1 = block-diagonal (one dense LU per panel block).
+ * report[host] (may be NULL): iterations, final relative residual, flags.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ENOCONV, BIE_ENAN, BIE_ECUDA.           */
+typedef struct {
+  double tol;
+  int restart;
+  int maxit;
+  int prec;
+  int precond;
+} bie_solve_opts;
+typedef struct {
+  int iterations;        /* total inner iterations over all right-hand sides */
+  int refinements;       /* outer FP64 refinement steps (prec = 1)            */
+  double rel_residual;   /* max over right-hand sides, FP64 residual          */
+  double seconds;        /* wall time of the call                             */
+} bie_solve_report;
+bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const double* rhs, int nrhs,
+                     double* x, const bie_solve_opts* opts, bie_solve_report* report);
+
+/* ---- boundary data and fields (Section 3.4, Section 5) ---------------------
+ * bie_rhs: g on the collocation nodes.  kind 0: plane wave, sound-soft,
+ * g = -e^{ik d.x} (param = d[3]); kind 1: point source g = G(x; x_src)
+ * (param = x_src[3]).  g [dev] double2[N].                                    */
+bie_status bie_rhs(bie_ctx ctx, bie_surface s, int kind, const double* param, double k, double* g);
+
+/* bie_field_eval: u(x_p) (far_field = 0) or the far-field pattern u_inf(d_p)
+ * (far_field = 1) of the representation rep (BIE_OP_S: single layer;
+ * BIE_OP_K: double layer; BIE_OP_CFIE: double layer - i eta single layer)
+ * with weighted density [dev] double2[N]; 16-point Gauss-Legendre in t times
+ * the trapezoid rule in theta; points assumed well separated from the surface.
+ *   pts [dev] double[n][3];  out [dev] double2[n].                            */
+bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep, double k, double eta,
+                          const double* density, const double* pts, int64_t n, int far_field,
+                          double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIE_H */

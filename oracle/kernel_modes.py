@@ -34,7 +34,7 @@ import numpy as np
 from . import geometry as geo
 from . import special as sp
 
-STABLE_DELTA = 0.25     # |t - t_s| + |th - th_s| below which differences use the line integral
+STABLE_DELTA = 0.06     # |t - t_s| + |th - th_s| below which differences use the line integral
 ROOT_TOL = 1e-14        # Newton stops when |dzeta| <= ROOT_TOL*b + 4e-16|zeta| (then one more step)
 SERIES_X = 0.5          # alpha(rho), beta(rho) use their Taylor series when k rho < SERIES_X
 SMALL_B = 0.1           # translated swapping for tau_3 when b < SMALL_B (the paper uses 0.01)
@@ -111,7 +111,13 @@ def locate_root(surface, t, th, t_s, thq, rho2):
     """a0, b0 and the Newton root (a, b) of rho^2(zeta) nearest to the real axis."""
     B, Mt = rho2.shape
     h = 2 * np.pi / Mt
-    q = np.argmin(rho2, axis=1)
+    # grid minimiser; near-ties (within 1e-12) go to the sample nearest the target angle
+    # (integer grid distance), then to the lower index, so rounding cannot pick a mirror root
+    i_t = np.rint(th * Mt / (2 * np.pi)).astype(int) % Mt
+    qq = np.arange(Mt)[None, :]
+    dist = np.minimum(np.abs(qq - i_t[:, None]), Mt - np.abs(qq - i_t[:, None]))
+    cand = rho2 <= rho2.min(axis=1, keepdims=True) * (1 + 1e-12)
+    q = np.argmin(np.where(cand, dist * Mt + qq, 4 * Mt * Mt), axis=1)
     a0 = thq[q].copy()
     start = a0.copy()
 

@@ -1,0 +1,95 @@
+// Context, status and error reporting of the C ABI.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+
+#include "bie_internal.cuh"
+
+namespace bie {
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+bie_status cuda_fail(cudaError_t e, const char* where) {
+  set_error("%s: %s", where, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BIE_ENOMEM : BIE_ECUDA;
+}
+
+// 16-point Gauss-Legendre nodes and weights on [0, 1] by Newton's method on P_16.
+GL16 gl16_unit() {
+  GL16 g;
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    long double x = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+    long double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1);
+      long double dx = p1 / dp;
+      x -= dx;
+      if (fabsl(dx) < 1e-19L) break;
+    }
+    // ascending order on [-1, 1]
+    g.x[n - 1 - i] = (double)((x + 1) / 2);
+    g.w[n - 1 - i] = (double)(1.0L / ((1 - x * x) * dp * dp));
+  }
+  return g;
+}
+}  // namespace bie
+
+extern "C" {
+
+const char* bie_last_error(void) { return bie::g_err; }
+
+bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream) {
+  if (!out) {
+    bie::set_error("bie_ctx_create: out is NULL");
+    return BIE_EINVAL;
+  }
+  bie_ctx c = new bie_ctx_s();
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { delete c; return bie::cuda_fail(e, "cudaGetDevice"); }
+  e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) { delete c; return bie::cuda_fail(e, "cudaDeviceGetAttribute"); }
+  e = cudaMalloc(&c->d_status, sizeof(int) * 4);
+  if (e != cudaSuccess) { delete c; return bie::cuda_fail(e, "cudaMalloc(status)"); }
+  e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) { cudaFree(c->d_status); delete c; return bie::cuda_fail(e, "cudaMemset(status)"); }
+  *out = c;
+  return BIE_OK;
+}
+
+void bie_ctx_free(bie_ctx ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+bie_status bie_ctx_sync(bie_ctx ctx) {
+  if (!ctx) { bie::set_error("bie_ctx_sync: NULL context"); return BIE_EINVAL; }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bie::cuda_fail(e, "cudaStreamSynchronize");
+  int st[4];
+  e = cudaMemcpy(st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bie::cuda_fail(e, "status readback");
+  if (st[0]) {
+    bie::set_error("device reported invalid pairs (%d)", st[0]);
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
+    return BIE_EINVAL;
+  }
+  return BIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,344 @@
+// Internal device helpers of the B300 surface-BIE library.
+//   * complex arithmetic on double2
+//   * analytic surfaces r(t, th) with first and second derivatives, for real
+//     theta and for complex theta (analytic continuation, Section 3.3)
+//   * cancellation-free differences r(v) - r(u) by the straight-path line
+//     integral of the first derivatives (Section 4, Remark), 16-point
+//     Gauss-Legendre
+//   * warp-cooperative mixed-radix (4, 2, 3) Stockham FFT in shared memory
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bie.h"
+
+namespace bie {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTwoPi = 6.283185307179586476925286766559005768;
+constexpr double kStableDelta = 0.06;  // |t - t_s| + |th - th_s| below which differences use the line integral
+constexpr double kRootTol = 1e-14;     // Newton stops when |dz| <= tol*b + 4e-16|z| (then one more step)
+constexpr double kSeriesX = 0.5;       // alpha, beta by Taylor series when k rho < this
+constexpr double kSmallB = 0.1;        // translated swapping for tau_3 when b < this
+constexpr double kNearPhi = 0.05;      // |th_q - a| below which the translated remainder uses the stable sum
+constexpr double kBCap = 4.0;          // roots farther than this from the real axis: (a0, kBCap)
+constexpr double kForwardLimit = 7.0;  // A_m: forward difference recurrence when L*b <= this
+constexpr double kMillerLog = 39.2;    // Miller start N = L + ceil(kMillerLog/(2b)) + 16
+
+// ------------------------------------------------------------------ complex
+struct cplx {
+  double re, im;
+};
+__host__ __device__ __forceinline__ cplx C(double r, double i = 0.0) { return {r, i}; }
+__host__ __device__ __forceinline__ cplx operator+(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a) { return {-a.re, -a.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, double s) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cplx conj(cplx a) { return {a.re, -a.im}; }
+__host__ __device__ __forceinline__ double abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  double d = 1.0 / (b.re * b.re + b.im * b.im);
+  return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
+__device__ __forceinline__ cplx cexpi(double x) {
+  double s, c;
+  sincos(x, &s, &c);
+  return {c, s};
+}
+// cos and sin of a complex argument
+__device__ __forceinline__ void ccossin(cplx z, cplx* c, cplx* s) {
+  double sx, cx;
+  sincos(z.re, &sx, &cx);
+  double ch = cosh(z.im), sh = sinh(z.im);
+  *c = {cx * ch, -sx * sh};
+  *s = {sx * ch, cx * sh};
+}
+__device__ __forceinline__ cplx shfl(cplx v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+// ------------------------------------------------------------------ surfaces
+struct SurfP {
+  int kind;       // 0 ellipsoid, 1 star
+  int nt;         // number of star terms
+  double ax, ay, az;
+  double c[BIE_MAX_TERMS];
+  int8_t p[BIE_MAX_TERMS], q[BIE_MAX_TERMS], m[BIE_MAX_TERMS], s[BIE_MAX_TERMS];
+};
+
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+using R3 = V3<double>;
+using C3 = V3<cplx>;
+
+__device__ __forceinline__ double dot(const R3& a, const R3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ R3 cross(const R3& a, const R3& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// sin^p cos^q and its first two t-derivatives
+__device__ __forceinline__ double scpow(double st, double ct, int p, int q) {
+  double v = 1.0;
+  for (int i = 0; i < p; ++i) v *= st;
+  for (int i = 0; i < q; ++i) v *= ct;
+  return v;
+}
+__device__ __forceinline__ void scpow_d(double st, double ct, int p, int q, double* g, double* gt, double* gtt) {
+  *g = scpow(st, ct, p, q);
+  double d1 = 0.0, d2 = 0.0;
+  if (p) d1 += p * scpow(st, ct, p - 1, q + 1);
+  if (q) d1 -= q * scpow(st, ct, p + 1, q - 1);
+  if (p) {
+    if (p > 1) d2 += p * (p - 1) * scpow(st, ct, p - 2, q + 2);
+    d2 -= p * (q + 1) * scpow(st, ct, p, q);
+  }
+  if (q) {
+    d2 -= q * (p + 1) * scpow(st, ct, p, q);
+    if (q > 1) d2 += q * (q - 1) * scpow(st, ct, p + 2, q - 2);
+  }
+  *gt = d1;
+  *gtt = d2;
+}
+
+// Surface point and derivatives at real (t, th).  order: 0 -> r; 1 -> r, rt, rth;
+// 2 -> also rtt, rtth, rthth.
+struct Geo {
+  R3 r, rt, rth, rtt, rtth, rthth;
+};
+__device__ inline void surf_eval(const SurfP& S, double t, double th, int order, Geo* g) {
+  double st, ct, sp, cp;
+  sincos(t, &st, &ct);
+  sincos(th, &sp, &cp);
+  if (S.kind == 0) {
+    g->r = {S.ax * st * cp, S.ay * st * sp, S.az * ct};
+    if (order >= 1) {
+      g->rt = {S.ax * ct * cp, S.ay * ct * sp, -S.az * st};
+      g->rth = {-S.ax * st * sp, S.ay * st * cp, 0.0};
+    }
+    if (order >= 2) {
+      g->rtt = {-S.ax * st * cp, -S.ay * st * sp, -S.az * ct};
+      g->rtth = {-S.ax * ct * sp, S.ay * ct * cp, 0.0};
+      g->rthth = {-S.ax * st * cp, -S.ay * st * sp, 0.0};
+    }
+    return;
+  }
+  double h = 1.0, ht = 0.0, hth = 0.0, htt = 0.0, htth = 0.0, hthth = 0.0;
+  for (int i = 0; i < S.nt; ++i) {
+    double gg, gt, gtt, sm, cm;
+    scpow_d(st, ct, S.p[i], S.q[i], &gg, &gt, &gtt);
+    const double mm = S.m[i];
+    sincos(mm * th, &sm, &cm);
+    double T, Tth, Tthth;
+    if (S.s[i] == 0) {
+      T = cm; Tth = -mm * sm; Tthth = -mm * mm * cm;
+    } else {
+      T = sm; Tth = mm * cm; Tthth = -mm * mm * sm;
+    }
+    const double c = S.c[i];
+    h += c * gg * T;
+    ht += c * gt * T;
+    hth += c * gg * Tth;
+    htt += c * gtt * T;
+    htth += c * gt * Tth;
+    hthth += c * gg * Tthth;
+  }
+  R3 e = {st * cp, st * sp, ct};
+  R3 et = {ct * cp, ct * sp, -st};
+  R3 eth = {-st * sp, st * cp, 0.0};
+  g->r = {h * e.x, h * e.y, h * e.z};
+  if (order >= 1) {
+    g->rt = {ht * e.x + h * et.x, ht * e.y + h * et.y, ht * e.z + h * et.z};
+    g->rth = {hth * e.x + h * eth.x, hth * e.y + h * eth.y, hth * e.z + h * eth.z};
+  }
+  if (order >= 2) {
+    R3 etth = {-ct * sp, ct * cp, 0.0};
+    R3 ethth = {-st * cp, -st * sp, 0.0};
+    g->rtt = {htt * e.x + 2 * ht * et.x - h * e.x, htt * e.y + 2 * ht * et.y - h * e.y,
+              htt * e.z + 2 * ht * et.z - h * e.z};
+    g->rtth = {htth * e.x + ht * eth.x + hth * et.x + h * etth.x, htth * e.y + ht * eth.y + hth * et.y + h * etth.y,
+               htth * e.z + ht * eth.z + hth * et.z + h * etth.z};
+    g->rthth = {hthth * e.x + 2 * hth * eth.x + h * ethth.x, hthth * e.y + 2 * hth * eth.y + h * ethth.y,
+                hthth * e.z + 2 * hth * eth.z + h * ethth.z};
+  }
+}
+
+// r, r_t, r_th at real t and complex th (analytic continuation in theta).
+__device__ inline void surf_eval_c(const SurfP& S, double t, cplx th, C3* r, C3* rt, C3* rth) {
+  double st, ct;
+  sincos(t, &st, &ct);
+  cplx cp, sp;
+  ccossin(th, &cp, &sp);
+  if (S.kind == 0) {
+    *r = {S.ax * st * cp, S.ay * st * sp, C(S.az * ct)};
+    *rt = {S.ax * ct * cp, S.ay * ct * sp, C(-S.az * st)};
+    *rth = {-S.ax * st * sp, S.ay * st * cp, C(0.0)};
+    return;
+  }
+  cplx h = C(1.0), ht = C(0.0), hth = C(0.0);
+  for (int i = 0; i < S.nt; ++i) {
+    double gg, gt, gtt;
+    scpow_d(st, ct, S.p[i], S.q[i], &gg, &gt, &gtt);
+    const double mm = S.m[i];
+    cplx cm, sm;
+    ccossin(mm * th, &cm, &sm);
+    cplx T, Tth;
+    if (S.s[i] == 0) {
+      T = cm; Tth = -mm * sm;
+    } else {
+      T = sm; Tth = mm * cm;
+    }
+    h = h + (S.c[i] * gg) * T;
+    ht = ht + (S.c[i] * gt) * T;
+    hth = hth + (S.c[i] * gg) * Tth;
+  }
+  C3 e = {st * cp, st * sp, C(ct)};
+  C3 et = {ct * cp, ct * sp, C(-st)};
+  C3 eth = {-st * sp, st * cp, C(0.0)};
+  *r = {h * e.x, h * e.y, h * e.z};
+  *rt = {ht * e.x + h * et.x, ht * e.y + h * et.y, ht * e.z + h * et.z};
+  *rth = {hth * e.x + h * eth.x, hth * e.y + h * eth.y, hth * e.z + h * eth.z};
+}
+
+// 16-point Gauss-Legendre on [0, 1] (nodes and weights), filled by the host.
+struct GL16 {
+  double x[16], w[16];
+};
+
+__device__ __forceinline__ double wrap_pi(double d) { return d - kTwoPi * rint(d / kTwoPi); }
+
+// r(t_s, th_s) - r(t, th) for complex th_s by the line integral of the first
+// derivatives along gamma(lam) = v + lam (u - v) (Section 4, Remark).
+__device__ inline C3 path_difference_c(const SurfP& S, const GL16& gl, double ts, cplx ths, double t, double th) {
+  const double dt = t - ts;
+  cplx dth = C(wrap_pi(th - ths.re), -ths.im);
+  C3 acc = {C(0), C(0), C(0)};
+  for (int j = 0; j < 16; ++j) {
+    C3 r, rt, rth;
+    surf_eval_c(S, ts + gl.x[j] * dt, ths + gl.x[j] * dth, &r, &rt, &rth);
+    const double w = gl.w[j];
+    acc.x = acc.x + w * (dt * rt.x + rth.x * dth);
+    acc.y = acc.y + w * (dt * rt.y + rth.y * dth);
+    acc.z = acc.z + w * (dt * rt.z + rth.z * dth);
+  }
+  return {-acc.x, -acc.y, -acc.z};
+}
+
+// ------------------------------------------------------------------ FFT
+// Twiddle table for length T (a multiple of every transform length used):
+// tw[k] = e^{-2 pi i k / T}.  A length-n transform uses index k*(T/n).
+struct FFTPlan {
+  int n;
+  int nst;
+  int rad[16];
+};
+
+__host__ __device__ inline FFTPlan make_plan(int n) {
+  FFTPlan p;
+  p.n = n;
+  p.nst = 0;
+  int m = n;
+  while (m % 4 == 0) { p.rad[p.nst++] = 4; m /= 4; }
+  while (m % 2 == 0) { p.rad[p.nst++] = 2; m /= 2; }
+  while (m % 3 == 0) { p.rad[p.nst++] = 3; m /= 3; }
+  if (m != 1) p.nst = -1;
+  return p;
+}
+
+// In-place (returns pointer to the buffer holding the result) transform of x[0..n)
+// using y as scratch.  sign = -1: X_k = sum x_j e^{-2 pi i jk/n}; sign = +1: inverse
+// (unnormalised).  Called by all 32 lanes of a warp.
+__device__ inline cplx* warp_fft(cplx* x, cplx* y, int n, const cplx* __restrict__ tw, int T, int sign) {
+  const int lane = threadIdx.x & 31;
+  const FFTPlan p = make_plan(n);
+  cplx* src = x;
+  cplx* dst = y;
+  int Ns = 1;
+  const double s3 = 0.86602540378443864676 * sign;
+  for (int st = 0; st < p.nst; ++st) {
+    const int R = p.rad[st];
+    const int stride = n / R;
+    const int tstep = (T / n) * (n / (Ns * R));  // table index step per (r * jm)
+    for (int j = lane; j < stride; j += 32) {
+      const int jm = j % Ns;
+      cplx v[4];
+      for (int r = 0; r < R; ++r) {
+        cplx a = src[j + r * stride];
+        if (r && jm) {
+          const double2 w2 = __ldg(reinterpret_cast<const double2*>(tw) + (r * jm * tstep) % T);
+          cplx w = C(w2.x, sign > 0 ? -w2.y : w2.y);
+          a = a * w;
+        }
+        v[r] = a;
+      }
+      cplx o[4];
+      if (R == 4) {
+        cplx s02 = v[0] + v[2], d02 = v[0] - v[2], s13 = v[1] + v[3], d13 = v[1] - v[3];
+        cplx jd = sign < 0 ? C(d13.im, -d13.re) : C(-d13.im, d13.re);  // sign*i*d13
+        o[0] = s02 + s13;
+        o[2] = s02 - s13;
+        o[1] = d02 + jd;
+        o[3] = d02 - jd;
+      } else if (R == 2) {
+        o[0] = v[0] + v[1];
+        o[1] = v[0] - v[1];
+      } else {
+        cplx t1 = v[1] + v[2], d = v[1] - v[2];
+        cplx t2 = C(-s3 * d.im, s3 * d.re);
+        cplx base = v[0] - 0.5 * t1;
+        o[0] = v[0] + t1;
+        o[1] = base + t2;
+        o[2] = base - t2;
+      }
+      const int idx = (j / Ns) * Ns * R + jm;
+      for (int r = 0; r < R; ++r) dst[idx + r * Ns] = o[r];
+    }
+    __syncwarp();
+    cplx* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= R;
+  }
+  return src;
+}
+
+}  // namespace bie
+
+// Opaque handles (host side)
+struct bie_ctx_s {
+  cudaStream_t stream;
+  int device;
+  int sms;
+  int* d_status;       // device status word (error flags from kernels)
+};
+
+struct bie_surface_s {
+  bie_ctx ctx;
+  bie::SurfP sp;
+  int Np, Mt;
+  double L, h;
+  int64_t N, n_rings;
+  double* t_nodes;     // [dev] [16 Np]
+  double* pts;         // [dev] [N][3]
+  double* nrm;         // [dev] [N][3]
+  double* jac;         // [dev] [N]
+  double* ring_t;      // [dev] [n_rings]
+  double* ring_r;      // [dev] [n_rings][Mt][3]
+  double* ring_n;      // [dev] [n_rings][Mt][3]
+  double* near_coef;   // [dev] [3][16][16][16] = w_g L_n(x_g) on the reference panel
+  double* ggq_x;       // [dev] [3][16][16]
+  bie::cplx* tw;       // [dev] twiddles for length 12 Mt
+  int tw_len;
+  double* host_t_nodes;
+};
+
+namespace bie {
+void set_error(const char* fmt, ...);
+bie_status cuda_fail(cudaError_t e, const char* where);
+GL16 gl16_unit();
+}  // namespace bie
