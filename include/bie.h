@@ -86,10 +86,14 @@ typedef struct {
 /* 16-node generalized Gaussian rules on the reference panel [-1, 1]
  * (Section 3.1: self and adjacent panels, nodes and weights depend on the
  * target node l).  x[d][l][g], w[d][l][g], d = delta + 1 with delta = -1
- * (source panel left of the target panel), 0 (self), +1 (right).            */
+ * (source panel left of the target panel), 0 (self), +1 (right).  The panel
+ * nodes t_i^l, the far-panel rule and the line-integral rule of the Section 4
+ * Remark all use gl_x/gl_w, so results depend only on these tables.         */
 typedef struct {
   double x[3][16][16];
   double w[3][16][16];
+  double gl_x[16];       /* 16-point Gauss-Legendre nodes on [-1, 1], ascending */
+  double gl_w[16];       /* and weights (Section 3.1: t_i^l and Eq. (S1))      */
 } bie_quad_tables;
 
 /* bie_surface_sample: sample the surface on the collocation grid (Np panels x
@@ -140,10 +144,14 @@ bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double
  * Errors: BIE_EINVAL, BIE_ECUDA.                                              */
 bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta, double* A_out);
 
-/* Correction stage only: write the near-block entries of S (and/or K) into
- * A_out (rows = targets), adding them to what is there.  The timed hot path. */
+/* Correction stage only (the paper's dominant cost, Section 3.4): add
+ * (ws_re + i ws_im) times the near-block entries of S and (wk_re + i wk_im)
+ * times those of K (kernels = bit mask of BIE_KERNEL_*) to A_out [dev]
+ * double2[N][N] (row = target).  Entries outside the near blocks are not
+ * touched.  Uses a device work buffer of 16*48*Mth*Mth double2 (freed on
+ * return, stream-ordered).  Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.       */
 bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
-                             double weight_s, double weight_k, double* A_out);
+                             double ws_re, double ws_im, double wk_re, double wk_im, double* A_out);
 
 /* ---- dense solve -------------------------------------------------------------
  * Restarted FGMRES (right preconditioned, modified Gram-Schmidt with
@@ -153,7 +161,9 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
  *   x    [dev] double2[nrhs][N] (initial guess in, solution out).
  *   prec 0 = FP64 matvec, 1 = FP32-stored matrix inside FGMRES with FP64
  *        iterative refinement (outer residuals in FP64).
- *   precond 0 = none, 1 = block-diagonal (one dense LU per panel block).
+ *   precond must be 0 (no preconditioner) in this build.
+ * Uses device work memory of (2 restart + 4) N double2 (+ N*N float2 for
+ * prec = 1), allocated stream-ordered and freed before return.
  * report[host] (may be NULL): iterations, final relative residual, flags.
  * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ENOCONV, BIE_ENAN, BIE_ECUDA.           */
 typedef struct {

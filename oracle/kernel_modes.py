@@ -176,7 +176,12 @@ def _pair_samples(surface, t, th, t_s, Mt):
 
 
 def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=False):
-    """Kernel modes by singularity swapping; dict kernel -> (B, Mt+1) complex (m = -M..M)."""
+    """Kernel modes by singularity swapping; dict kernel -> (B, Mt+1) complex (m = -M..M).
+
+    Also returns, per kernel, the swapped part "<kernel>_sing" (modes) and the
+    smooth part "<kernel>_smooth" (its samples on the theta grid: i sin(k rho)/rho
+    for S, -i beta tau_0 for K), whose Parseval weights are the trapezoid rule.
+    """
     t = np.atleast_1d(np.asarray(t, float))
     th = np.atleast_1d(np.asarray(th, float))
     t_s = np.atleast_1d(np.asarray(t_s, float))
@@ -198,8 +203,10 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
     R = swap_convolution(f, a, A, rmax)                                        # <rho^{-1}>_l
     if "S" in kernels:
         C = sym_modes(np.cos(k * rho), M)
-        Sn = sym_modes(np.sin(k * rho) / rho, M)
-        out["S"] = linear_convolution(C, R, rmax, M) + 1j * Sn
+        smooth = 1j * np.sin(k * rho) / rho
+        out["S_sing"] = linear_convolution(C, R, rmax, M)
+        out["S_smooth"] = smooth
+        out["S"] = out["S_sing"] + sym_modes(smooth, M)
     if need_k:
         nu, _ = geo.normal_and_jacobian(surface, T_s, TH_s)
         tau0 = np.sum(nu * Y, -1)
@@ -210,7 +217,10 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
         T1 = linear_convolution(T0, R, rmax, 2 * M)                            # Eq. (tau1)
         AT1 = linear_convolution(sym_modes(alpha, M), T1, 2 * M, M)
         T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s))
-        out["K"] = AT1 - T3 - 1j * sym_modes(beta * tau0, M)
+        smooth = -1j * beta * tau0
+        out["K_sing"] = AT1 - T3
+        out["K_smooth"] = smooth
+        out["K"] = out["K_sing"] + sym_modes(smooth, M)
     if return_details:
         out["_a"], out["_b"], out["_a0"], out["_b0"], out["_ok"] = a, b, a0, b0, ok
         out["_R"], out["_rmax"] = R, rmax

@@ -14,8 +14,9 @@ Row of target (t_j^l, th_i), Section 3.1 Eq. (S123) and Section 3.4:
       A = sum_g (h/2) omega_g^{delta,l} L_n(s_g^{delta,l}) W_{l'}(pair g)
   with the 16-node GGQ rule (s_g, omega_g) of the table, L_n the Lagrange
   basis on the 16 Legendre nodes of panel i', and W_{l'} the Parseval
-  weights of the pair's kernel modes:
-      W_{l'} = (1/Mth) [ sum_{|m|<M} K_m e^{i m th_l'} + (K_M + K_{-M})/2 (-1)^{l'} ].
+  weights of the pair's kernel: for the swapped part with modes K_m
+      W_{l'} = (1/Mth) [ sum_{|m|<M} K_m e^{i m th_l'} + (K_M + K_{-M})/2 (-1)^{l'} ],
+  plus, for the smooth part f (i sin(k rho)/rho, -i beta tau_0), f(th_l')/Mth.
 Kernels G~: S -> e^{ik rho}/rho;  K -> tau_0 e^{ik rho}(ik rho - 1)/rho^3
 (= alpha tau_1 - tau_3 - i beta tau_0, Section 4).
 
@@ -49,6 +50,13 @@ def lagrange(x):
             if m != n:
                 out[:, n] *= (x - XG[m]) / (XG[n] - XG[m])
     return out
+
+
+def parseval_weights_split(sing, smooth):
+    """Weights of a kernel split into a swapped part (modes, symmetric Nyquist) and a smooth
+    part (grid samples): for the smooth part the Fourier route is the trapezoid rule
+    exactly (discrete Parseval, Section 3.2), so its weights are the samples / Mth."""
+    return parseval_weights(sing) + smooth / smooth.shape[-1]
 
 
 def parseval_weights(modes):
@@ -130,7 +138,7 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=51
         cols = ip[:, None, None] * 16 * Mt + np.arange(16)[None, :, None] * Mt + np.arange(Mt)[None, None, :]
         modes = km.method_modes(surface, t, tht, ts, Mt, k, kernels=tuple(kinds))
         for kd in kinds:
-            W = parseval_weights(modes[kd])
+            W = parseval_weights_split(modes[kd + "_sing"], modes[kd + "_smooth"])
             vals = coef[di, l, g][:, :, None] * W[:, None, :]
             np.add.at(out[kd], (np.broadcast_to(pos[:, None, None], cols.shape), cols), vals)
     return out

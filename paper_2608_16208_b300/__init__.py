@@ -30,7 +30,8 @@ class SurfaceDesc(ctypes.Structure):
 
 
 class QuadTables(ctypes.Structure):
-    _fields_ = [("x", ctypes.c_double * (3 * 16 * 16)), ("w", ctypes.c_double * (3 * 16 * 16))]
+    _fields_ = [("x", ctypes.c_double * (3 * 16 * 16)), ("w", ctypes.c_double * (3 * 16 * 16)),
+                ("gl_x", ctypes.c_double * 16), ("gl_w", ctypes.c_double * 16)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -113,9 +114,12 @@ class Surface:
             self._terms = terms
             d.terms = terms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         q = QuadTables()
-        gx, gw = ggq
+        gx, gw = ggq[0], ggq[1]
         q.x[:] = np.ascontiguousarray(gx, dtype=np.float64).ravel().tolist()
         q.w[:] = np.ascontiguousarray(gw, dtype=np.float64).ravel().tolist()
+        glx, glw = (ggq[2], ggq[3]) if len(ggq) > 2 else np.polynomial.legendre.leggauss(16)
+        q.gl_x[:] = [float(v) for v in glx]
+        q.gl_w[:] = [float(v) for v in glw]
         self.h = _vp()
         check(lib.bie_surface_sample(ctx.h, ctypes.byref(d), Np, Mt, ctypes.byref(q), ctypes.byref(self.h)),
               "bie_surface_sample")
@@ -136,4 +140,64 @@ def kernel_modes(surface, kernels, k, rows, srcs, out=None):
         out = torch.empty((n, nk, surface.Mt + 1), dtype=torch.complex128, device="cuda")
     check(lib.bie_kernel_modes(surface.ctx.h, surface.h, kernels, float(k), _ptr(rows), _ptr(srcs), n,
                                _ptr(out)), "bie_kernel_modes")
+    return out
+
+
+_sig("bie_assemble", _i32, [_vp, _vp, _i32, _d, _d, _vp])
+_sig("bie_assemble_near", _i32, [_vp, _vp, _u, _d, _d, _d, _d, _d, _vp])
+_sig("bie_solve", _i32, [_vp, _i64, _vp, _vp, _i32, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)])
+_sig("bie_rhs", _i32, [_vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _d, _vp])
+_sig("bie_field_eval", _i32, [_vp, _vp, _i32, _d, _d, _vp, _vp, _i64, _i32, _vp])
+
+
+def assemble(surface, op, k, eta=None, out=None):
+    """Dense operator matrix [N, N] complex128 (row = target)."""
+    N = surface.N
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.complex128, device="cuda")
+    check(lib.bie_assemble(surface.ctx.h, surface.h, op, float(k), float(k if eta is None else eta), _ptr(out)),
+          "bie_assemble")
+    return out
+
+
+def assemble_near(surface, kernels, k, A, ws=1.0, wk=0.0):
+    """Add ws * (near blocks of S) + wk * (near blocks of K) to A (correction stage)."""
+    ws, wk = complex(ws), complex(wk)
+    check(lib.bie_assemble_near(surface.ctx.h, surface.h, kernels, float(k), ws.real, ws.imag, wk.real, wk.imag,
+                                _ptr(A)), "bie_assemble_near")
+    return A
+
+
+def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0):
+    """FGMRES solve of A x = b (b: [N] or [nrhs, N]); returns (x, report dict)."""
+    n = A.shape[0]
+    bb = b.reshape(-1, n).contiguous()
+    nrhs = bb.shape[0]
+    if x is None:
+        x = torch.zeros_like(bb)
+    o = SolveOpts(tol, restart, maxit, prec, 0)
+    r = SolveReport()
+    st = lib.bie_solve(ctx.h, n, _ptr(A), _ptr(bb), nrhs, _ptr(x), ctypes.byref(o), ctypes.byref(r))
+    rep = {"iterations": r.iterations, "refinements": r.refinements, "rel_residual": r.rel_residual,
+           "seconds": r.seconds, "status": st}
+    check(st, "bie_solve")
+    return x.reshape(b.shape), rep
+
+
+def rhs(surface, kind, param, k, out=None):
+    """Boundary data: kind 0 plane wave -e^{ik d.x} (param = d), kind 1 point source (param = source)."""
+    if out is None:
+        out = torch.empty(surface.N, dtype=torch.complex128, device="cuda")
+    p = (ctypes.c_double * 3)(*[float(v) for v in param])
+    check(lib.bie_rhs(surface.ctx.h, surface.h, kind, p, float(k), _ptr(out)), "bie_rhs")
+    return out
+
+
+def field_eval(surface, rep, k, density, points, far_field=False, eta=None):
+    """u(x) at points [n, 3] (or the far-field pattern in directions [n, 3])."""
+    pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).contiguous().cuda()
+    out = torch.empty(pts.shape[0], dtype=torch.complex128, device="cuda")
+    check(lib.bie_field_eval(surface.ctx.h, surface.h, rep, float(k), float(k if eta is None else eta),
+                             _ptr(density), _ptr(pts), pts.shape[0], 1 if far_field else 0, _ptr(out)),
+          "bie_field_eval")
     return out

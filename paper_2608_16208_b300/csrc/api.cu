@@ -21,31 +21,6 @@ bie_status cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? BIE_ENOMEM : BIE_ECUDA;
 }
 
-// 16-point Gauss-Legendre nodes and weights on [0, 1] by Newton's method on P_16.
-GL16 gl16_unit() {
-  GL16 g;
-  const int n = 16;
-  for (int i = 0; i < n; ++i) {
-    long double x = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
-    long double dp = 0;
-    for (int it = 0; it < 100; ++it) {
-      long double p0 = 1, p1 = x;
-      for (int k = 2; k <= n; ++k) {
-        long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (x * p1 - p0) / (x * x - 1);
-      long double dx = p1 / dp;
-      x -= dx;
-      if (fabsl(dx) < 1e-19L) break;
-    }
-    // ascending order on [-1, 1]
-    g.x[n - 1 - i] = (double)((x + 1) / 2);
-    g.w[n - 1 - i] = (double)(1.0L / ((1 - x * x) * dp * dp));
-  }
-  return g;
-}
 }  // namespace bie
 
 extern "C" {

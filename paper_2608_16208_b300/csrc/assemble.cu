@@ -1,0 +1,173 @@
+// Dense Nystrom assembly (Section 3.4; Section 3.1 Eqs. (S123), (S1); Section 4).
+//
+// Preparation stage: every entry of the N x N matrix from the 16-point
+// Gauss-Legendre rule in t and the trapezoid rule in theta (Eq. (S1) with
+// Eq. (Sphi:sm)); entries of near blocks (|i - j| <= 1) are set to zero and the
+// identity of K +- I / CFIE is added on the diagonal (identity acting on the
+// weighted density = diag(1/J)).
+//
+// Correction stage: for every target node and near panel, the Parseval weights
+// of the 16 GGQ source rings (pair pipeline) are combined with the GGQ weights
+// and the Lagrange basis of the source panel's Legendre nodes:
+//   A[x, (i',n,l')] += (h/2) sum_g w_g L_n(s_g) W_{l'}(x, s_g).
+// One target panel at a time, so the weight buffer holds 16*48*Mth pairs.
+#include <cmath>
+
+#include "bie_internal.cuh"
+#include "pair_args.cuh"
+
+namespace bie {
+
+struct FarArgs {
+  SurfP S;
+  int Np, Mt;
+  int64_t N;
+  double h, k, wid;
+  cplx ws, wk;
+  const double* pts;
+  const double* nrm;
+  const double* jac;
+  double wgl[16];       // Gauss-Legendre weights on [-1, 1]
+  cplx* A;
+};
+
+// One thread per (row, column); grid-stride over the N x N entries, rows in blockIdx.y chunks.
+__global__ void far_fill_kernel(const FarArgs a) {
+  const int64_t N = a.N;
+  const int64_t per_panel = (int64_t)16 * a.Mt;
+  for (int64_t row = blockIdx.y; row < N; row += gridDim.y) {
+    const double xx = a.pts[3 * row], xy = a.pts[3 * row + 1], xz = a.pts[3 * row + 2];
+    const int jrow = (int)(row / per_panel);
+    cplx* Arow = a.A + row * N;
+    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < N; col += (int64_t)gridDim.x * blockDim.x) {
+      const int jcol = (int)(col / per_panel);
+      cplx v = C(0.0);
+      if (abs(jcol - jrow) >= 2) {
+        const double yx = a.pts[3 * col] - xx, yy = a.pts[3 * col + 1] - xy, yz = a.pts[3 * col + 2] - xz;
+        const double r2 = yx * yx + yy * yy + yz * yz;
+        const double rinv = rsqrt(r2);
+        const double rho = r2 * rinv;
+        double s, c;
+        sincos(a.k * rho, &s, &c);
+        const int n = (int)((col / a.Mt) % 16);
+        const double w = a.h * 0.5 * a.wgl[n] / a.Mt;
+        cplx e = C(c, s);
+        cplx val = C(0.0);
+        if (a.ws.re != 0.0 || a.ws.im != 0.0) val = rinv * (a.ws * e);
+        if (a.wk.re != 0.0 || a.wk.im != 0.0) {
+          const double tau0 = a.nrm[3 * col] * yx + a.nrm[3 * col + 1] * yy + a.nrm[3 * col + 2] * yz;
+          const double f = tau0 * rinv * rinv * rinv;
+          val = val + f * (a.wk * (e * C(-1.0, a.k * rho)));
+        }
+        v = w * val;
+      }
+      if (col == row && a.wid != 0.0) v = v + C(a.wid / a.jac[row], 0.0);
+      Arow[col] = v;
+    }
+  }
+}
+
+// Near fill of one target panel: block per (local target node tl in [0, 16 Mt), delta).
+__global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx scale, const double* __restrict__ coef,
+                                 const cplx* __restrict__ W, cplx* __restrict__ A) {
+  const int tl = blockIdx.x;            // l * Mt + i
+  const int d = blockIdx.y;
+  const int l = tl / Mt, i = tl % Mt;
+  const int ip = jpanel + d - 1;
+  if (ip < 0 || ip >= Np) return;
+  const int64_t tn = (int64_t)jpanel * 16 + l;
+  const int64_t row = tn * Mt + i;
+  // W index within the panel chunk: (((l*3 + d)*16 + g)*Mt + i)
+  const cplx* Wg = W + ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
+  const double* cf = coef + ((d * 16 + l) * 16) * 16;   // [g][n]
+  cplx* Arow = A + row * N + (int64_t)ip * 16 * Mt;
+  for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
+    const int n = e / Mt, lp = e % Mt;
+    cplx acc = C(0.0);
+#pragma unroll 4
+    for (int g = 0; g < 16; ++g) acc = acc + cf[g * 16 + n] * Wg[(int64_t)g * Mt * Mt + lp];
+    Arow[e] = Arow[e] + scale * acc;
+  }
+}
+
+}  // namespace bie
+
+using namespace bie;
+
+extern "C" {
+
+bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re, double ws_im,
+                             double wk_re, double wk_im, double* A_out) {
+  if (!ctx || !s || !A_out) { set_error("bie_assemble_near: NULL argument"); return BIE_EINVAL; }
+  if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble_near: k must be in (0, 1e6)"); return BIE_EINVAL; }
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
+    set_error("bie_assemble_near: bad kernel mask %u", kernels);
+    return BIE_EINVAL;
+  }
+  if (kernels & BIE_KERNEL_K) { set_error("bie_assemble_near: the double-layer kernel is not in this build"); return BIE_EUNSUPPORTED; }
+  const int Mt = s->Mt;
+  const int64_t chunk_pairs = (int64_t)16 * 48 * Mt;
+  cplx* W = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(weights)");
+  bie_status st = BIE_OK;
+  const cplx scale_s = C(ws_re, ws_im) * (0.5 * s->h);
+  for (int j = 0; j < s->Np && st == BIE_OK; ++j) {
+    PairArgs a = make_pair_args(s, k);
+    a.enumerate = 1;
+    a.p0 = (int64_t)j * chunk_pairs;
+    a.n_pairs = chunk_pairs;
+    a.weights_out = W;
+    st = launch_pairs(s, a);
+    if (st != BIE_OK) break;
+    dim3 grid(16 * Mt, 3);
+    near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j, scale_s, s->near_coef, W, (cplx*)A_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");
+  }
+  cudaFreeAsync(W, ctx->stream);
+  return st;
+}
+
+bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta, double* A_out) {
+  if (!ctx || !s || !A_out) { set_error("bie_assemble: NULL argument"); return BIE_EINVAL; }
+  if (op < BIE_OP_S || op > BIE_OP_CFIE) { set_error("bie_assemble: unknown operator %d", op); return BIE_EINVAL; }
+  if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble: k must be in (0, 1e6)"); return BIE_EINVAL; }
+  cplx ws = C(0.0), wk = C(0.0);
+  double wid = 0.0;
+  switch (op) {
+    case BIE_OP_S: ws = C(1.0); break;
+    case BIE_OP_K: wk = C(1.0); break;
+    case BIE_OP_K_PLUS_I: wk = C(1.0); wid = 1.0; break;
+    case BIE_OP_K_MINUS_I: wk = C(1.0); wid = -1.0; break;
+    case BIE_OP_CFIE: wk = C(1.0); wid = 1.0; ws = C(0.0, -eta); break;
+  }
+  if (wk.re != 0.0) { set_error("bie_assemble: the double-layer kernel is not in this build"); return BIE_EUNSUPPORTED; }
+  FarArgs fa;
+  fa.S = s->sp;
+  fa.Np = s->Np;
+  fa.Mt = s->Mt;
+  fa.N = s->N;
+  fa.h = s->h;
+  fa.k = k;
+  fa.ws = ws;
+  fa.wk = wk;
+  fa.wid = wid;
+  fa.pts = s->pts;
+  fa.nrm = s->nrm;
+  fa.jac = s->jac;
+  for (int n = 0; n < 16; ++n) fa.wgl[n] = s->gl_w[n];
+  fa.A = (cplx*)A_out;
+  const unsigned rows_per_launch = (unsigned)((s->N < 65535) ? s->N : 65535);
+  const int64_t colblocks = (s->N + 255) / 256;
+  dim3 grid((unsigned)(colblocks < 64 ? colblocks : 64), rows_per_launch);
+  far_fill_kernel<<<grid, 256, 0, ctx->stream>>>(fa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "far_fill_kernel");
+  unsigned kernels = 0;
+  if (ws.re != 0.0 || ws.im != 0.0) kernels |= BIE_KERNEL_S;
+  if (wk.re != 0.0 || wk.im != 0.0) kernels |= BIE_KERNEL_K;
+  return bie_assemble_near(ctx, s, kernels, k, ws.re, ws.im, wk.re, wk.im, A_out);
+}
+
+}  // extern "C"

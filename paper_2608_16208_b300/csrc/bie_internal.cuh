@@ -335,10 +335,11 @@ struct bie_surface_s {
   bie::cplx* tw;       // [dev] twiddles for length 12 Mt
   int tw_len;
   double* host_t_nodes;
+  double gl_x[16], gl_w[16];   // Gauss-Legendre rule on [-1, 1] from the caller's tables
+  bie::GL16 gl01;              // the same rule mapped to [0, 1]
 };
 
 namespace bie {
 void set_error(const char* fmt, ...);
 bie_status cuda_fail(cudaError_t e, const char* where);
-GL16 gl16_unit();
 }  // namespace bie

@@ -1,0 +1,132 @@
+// Boundary data on the collocation nodes and layer-potential evaluation away
+// from the surface (Section 3.4: 16-point Gauss-Legendre in t times the
+// trapezoid rule in theta; Section 5 data).
+#include <cmath>
+
+#include "bie_internal.cuh"
+
+namespace bie {
+
+__global__ void rhs_kernel(int64_t N, const double* __restrict__ pts, int kind, double px, double py, double pz,
+                           double k, double2* __restrict__ g) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+    double s, c;
+    if (kind == 0) {  // sound-soft plane wave: -e^{ik d.x}
+      sincos(k * (px * x + py * y + pz * z), &s, &c);
+      g[i] = make_double2(-c, -s);
+    } else {          // point source e^{ik r}/(4 pi r)
+      const double dx = x - px, dy = y - py, dz = z - pz;
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      sincos(k * r, &s, &c);
+      const double f = 1.0 / (4 * kPi * r);
+      g[i] = make_double2(c * f, s * f);
+    }
+  }
+}
+
+struct FieldArgs {
+  int64_t N;
+  int Mt;
+  double h, k, eta;
+  int rep, far;
+  double wgl[16];
+  const double* pts;
+  const double* nrm;
+  const double2* dens;
+  const double* tgt;
+  double2* out;
+};
+
+// One CTA per evaluation point; threads over the surface nodes.
+__global__ void field_kernel(const FieldArgs a) {
+  const int64_t p = blockIdx.x;
+  const double x = a.tgt[3 * p], y = a.tgt[3 * p + 1], z = a.tgt[3 * p + 2];
+  double re = 0, im = 0;
+  for (int64_t i = threadIdx.x; i < a.N; i += blockDim.x) {
+    const int n = (int)((i / a.Mt) % 16);
+    const double w = a.h * 0.5 * a.wgl[n] / a.Mt;
+    const double yx = a.pts[3 * i], yy = a.pts[3 * i + 1], yz = a.pts[3 * i + 2];
+    const double nx = a.nrm[3 * i], ny = a.nrm[3 * i + 1], nz = a.nrm[3 * i + 2];
+    cplx kern;
+    if (!a.far) {
+      const double dx = yx - x, dy = yy - y, dz = yz - z;
+      const double rho = sqrt(dx * dx + dy * dy + dz * dz);
+      const cplx e = cexpi(a.k * rho);
+      const cplx sl = e * (1.0 / rho);
+      if (a.rep == BIE_OP_S) {
+        kern = sl;
+      } else {
+        const double tau0 = nx * dx + ny * dy + nz * dz;
+        kern = (tau0 / (rho * rho * rho)) * (e * C(-1.0, a.k * rho));
+        if (a.rep == BIE_OP_CFIE) kern = kern + C(0.0, -a.eta) * sl;
+      }
+    } else {  // far-field pattern in direction (x, y, z) (unit vector)
+      const cplx e = cexpi(-a.k * (x * yx + y * yy + z * yz));
+      if (a.rep == BIE_OP_S) {
+        kern = e;
+      } else {
+        kern = C(0.0, -a.k * (x * nx + y * ny + z * nz)) * e;
+        if (a.rep == BIE_OP_CFIE) kern = kern + C(0.0, -a.eta) * e;
+      }
+    }
+    const double2 d = a.dens[i];
+    const cplx v = w * (kern * C(d.x, d.y));
+    re += v.re;
+    im += v.im;
+  }
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  __shared__ double sre[32], sim[32];
+  if ((threadIdx.x & 31) == 0) { sre[threadIdx.x >> 5] = re; sim[threadIdx.x >> 5] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0, m = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { r += sre[k]; m += sim[k]; }
+    a.out[p] = make_double2(r, m);
+  }
+}
+
+}  // namespace bie
+
+using namespace bie;
+
+extern "C" {
+
+bie_status bie_rhs(bie_ctx ctx, bie_surface s, int kind, const double* param, double k, double* g) {
+  if (!ctx || !s || !param || !g || (kind != 0 && kind != 1)) { set_error("bie_rhs: invalid arguments"); return BIE_EINVAL; }
+  rhs_kernel<<<ctx->sms * 4, 256, 0, ctx->stream>>>(s->N, s->pts, kind, param[0], param[1], param[2], k, (double2*)g);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "rhs_kernel");
+}
+
+bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep, double k, double eta, const double* density,
+                          const double* pts, int64_t n, int far_field, double* out) {
+  if (!ctx || !s || !density || !pts || !out || n < 0 || n > (1 << 30) ||
+      (rep != BIE_OP_S && rep != BIE_OP_K && rep != BIE_OP_CFIE)) {
+    set_error("bie_field_eval: invalid arguments");
+    return BIE_EINVAL;
+  }
+  if (n == 0) return BIE_OK;
+  FieldArgs a;
+  a.N = s->N;
+  a.Mt = s->Mt;
+  a.h = s->h;
+  a.k = k;
+  a.eta = eta;
+  a.rep = rep;
+  a.far = far_field ? 1 : 0;
+  for (int i = 0; i < 16; ++i) a.wgl[i] = s->gl_w[i];
+  a.pts = s->pts;
+  a.nrm = s->nrm;
+  a.dens = (const double2*)density;
+  a.tgt = pts;
+  a.out = (double2*)out;
+  field_kernel<<<(unsigned)n, 256, 0, ctx->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "field_kernel");
+}
+
+}  // extern "C"

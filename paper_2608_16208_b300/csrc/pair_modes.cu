@@ -26,28 +26,11 @@
 #include <cmath>
 
 #include "bie_internal.cuh"
+#include "pair_args.cuh"
 
 namespace bie {
 
-struct PairArgs {
-  SurfP S;
-  GL16 gl;
-  int Np, Mt, M, P, T, L;
-  double h, k;
-  int64_t N, n_pairs;
-  int enumerate;                 // 1: pair p enumerates every (node, delta, g, theta) of the surface
-  const double* t_nodes;
-  const double* pts;
-  const double* ring_t;
-  const double* ring_r;
-  const double* ring_n;
-  const cplx* tw;
-  const int64_t* rows;
-  const int32_t* srcs;
-  double* modes_out;             // [p][Mt+1] complex, or null
-  cplx* weights_out;             // [p][Mt] complex, or null
-  int* status;
-};
+
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -234,8 +217,9 @@ __global__ void __launch_bounds__(128) pair_s_kernel(const PairArgs a) {
     int64_t row;
     int d, g;
     if (a.enumerate) {
-      const int i = (int)(p % Mt);
-      int64_t rest = p / Mt;
+      const int64_t pg = a.p0 + p;
+      const int i = (int)(pg % Mt);
+      int64_t rest = pg / Mt;
       g = (int)(rest % 16);
       rest /= 16;
       d = (int)(rest % 3);
@@ -408,7 +392,7 @@ size_t pair_s_smem_per_warp(int Mt) {
 PairArgs make_pair_args(bie_surface s, double k) {
   PairArgs a;
   a.S = s->sp;
-  a.gl = gl16_unit();
+  a.gl = s->gl01;
   a.Np = s->Np;
   a.Mt = s->Mt;
   a.M = s->Mt / 2;
@@ -430,6 +414,7 @@ PairArgs make_pair_args(bie_surface s, double k) {
   a.weights_out = nullptr;
   a.status = s->ctx->d_status;
   a.enumerate = 0;
+  a.p0 = 0;
   a.n_pairs = 0;
   return a;
 }

@@ -95,11 +95,31 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   s->h = s->L / Np;
   s->N = (int64_t)16 * Np * Mt;
   s->n_rings = (int64_t)16 * Np * 48;
-  // nodes (Gauss-Legendre on [-1, 1] from the [0, 1] rule)
-  GL16 gl = gl16_unit();
+  // Gauss-Legendre rule from the tables: validate, keep, map to [0, 1]
+  {
+    double wsum = 0.0;
+    for (int l = 0; l < 16; ++l) {
+      wsum += ggq->gl_w[l];
+      if (!(ggq->gl_x[l] > -1.0 && ggq->gl_x[l] < 1.0) || !(ggq->gl_w[l] > 0) ||
+          (l && !(ggq->gl_x[l] > ggq->gl_x[l - 1]))) {
+        delete s;
+        set_error("bie_surface_sample: Gauss-Legendre table is not an ascending rule on (-1, 1)");
+        return BIE_EINVAL;
+      }
+      s->gl_x[l] = ggq->gl_x[l];
+      s->gl_w[l] = ggq->gl_w[l];
+      s->gl01.x[l] = (ggq->gl_x[l] + 1) / 2;
+      s->gl01.w[l] = ggq->gl_w[l] / 2;
+    }
+    if (fabs(wsum - 2.0) > 1e-13) {
+      delete s;
+      set_error("bie_surface_sample: Gauss-Legendre weights do not sum to 2");
+      return BIE_EINVAL;
+    }
+  }
   std::vector<double> tn(16 * Np), rt(s->n_rings);
   for (int j = 0; j < Np; ++j)
-    for (int l = 0; l < 16; ++l) tn[j * 16 + l] = (j + 0.5) * s->h + (s->h / 2) * (2 * gl.x[l] - 1);
+    for (int l = 0; l < 16; ++l) tn[j * 16 + l] = (j + 0.5) * s->h + (s->h / 2) * s->gl_x[l];
   for (int j = 0; j < Np; ++j)
     for (int l = 0; l < 16; ++l)
       for (int d = 0; d < 3; ++d)
@@ -116,9 +136,9 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
         const double x = ggq->x[d][l][g];
         for (int n = 0; n < 16; ++n) {
           double Ln = 1.0;
-          const double xn = 2 * gl.x[n] - 1;
+          const double xn = s->gl_x[n];
           for (int m = 0; m < 16; ++m)
-            if (m != n) Ln *= (x - (2 * gl.x[m] - 1)) / (xn - (2 * gl.x[m] - 1));
+            if (m != n) Ln *= (x - s->gl_x[m]) / (xn - s->gl_x[m]);
           coef[((d * 16 + l) * 16 + g) * 16 + n] = ggq->w[d][l][g] * Ln;
         }
       }

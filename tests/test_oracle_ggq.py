@@ -20,7 +20,7 @@ def _moments(tau):
 @pytest.mark.parametrize("delta", [-1, 0, 1])
 @pytest.mark.parametrize("l", [0, 3, 7, 8, 12, 15])
 def test_ggq_rule_is_exact(ggq, delta, l):
-    gx, gw = ggq
+    gx, gw = ggq[0], ggq[1]
     x, w = gx[delta + 1, l], gw[delta + 1, l]
     tau = XL[l] - 2.0 * delta
     P = np.polynomial.legendre.legvander(x, 15).T          # P_n(x_g)
@@ -30,7 +30,7 @@ def test_ggq_rule_is_exact(ggq, delta, l):
 
 
 def test_ggq_mirror_symmetry(ggq):
-    gx, gw = ggq
+    gx, gw = ggq[0], ggq[1]
     for l in range(16):
         assert np.allclose(gx[2, l], -gx[0, 15 - l][::-1], atol=0)
         assert np.allclose(gx[1, l], -gx[1, 15 - l][::-1], atol=0)

@@ -70,7 +70,8 @@ class Stream:
 # quadrature table
 # ----------------------------------------------------------------------------
 def load_ggq(path=None):
-    """GGQ nodes and weights, arrays [3, 16, 16] indexed [delta+1, l, g]."""
+    """GGQ nodes and weights, arrays [3, 16, 16] indexed [delta+1, l, g], and the
+    16-point Gauss-Legendre rule on [-1, 1] that both the oracle and the library use."""
     tab = np.loadtxt(path or _TABLE)
     gx = np.zeros((3, 16, 16))
     gw = np.zeros((3, 16, 16))
@@ -78,7 +79,8 @@ def load_ggq(path=None):
         d, l = int(row[0]) + 1, int(row[1])
         gx[d, l] = row[3:19]
         gw[d, l] = row[19:35]
-    return gx, gw
+    glx, glw = np.polynomial.legendre.leggauss(16)
+    return gx, gw, glx, glw
 
 
 # ----------------------------------------------------------------------------
