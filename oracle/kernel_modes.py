@@ -216,7 +216,7 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
         T0 = sym_modes(tau0, M)
         T1 = linear_convolution(T0, R, rmax, 2 * M)                            # Eq. (tau1)
         AT1 = linear_convolution(sym_modes(alpha, M), T1, 2 * M, M)
-        T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s))
+        T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s, f))
         smooth = -1j * beta * tau0
         out["K_sing"] = AT1 - T3
         out["K_smooth"] = smooth
@@ -235,17 +235,21 @@ def tau3_modes(H3, a, b, A, D, M, pair):
     small = b < SMALL_B
     if np.any(small):
         i = np.nonzero(small)[0]
-        surface, t, th, t_s = pair
-        Ha, H1a = h3_at_root(surface, t[i], th[i], t_s[i], a[i], b[i])
+        surface, t, th, t_s, f = pair
+        Ha, H1a = h3_at_root(surface, t[i], th[i], t_s[i], a[i], b[i], f[i])
         out[i] = _tau3_translated(H3[i], h3[i], a[i], b[i], A[i], Bn[i], M, Ha, H1a)
     return out
 
 
-def h3_at_root(surface, t, th, t_s, a, b):
-    """H3(a) = tau_0(a) F(a)^3 and H3'(a), evaluated directly from the geometry at th_s = a.
+def h3_at_root(surface, t, th, t_s, a, b, f=None):
+    """H3(a) = tau_0(a) F(a)^3 and H3'(a), evaluated at th_s = a.
 
-    s_{a,b}(a) = (1 - e^{-b})^2 and s'(a) = 0, so F(a) = (1 - e^{-b}) / rho(a) and
-    F'(a) = -F(a) (rho^2)'(a) / (2 rho^2(a)); tau_0'(a) = nu'(a) . (r_s(a) - r).
+    tau_0(a), tau_0'(a) = nu'(a) . (r_s(a) - r) and F(a) = (1 - e^{-b}) / rho(a)
+    (s_{a,b}(a) = (1 - e^{-b})^2) come directly from the geometry: they are
+    small (O(b^2), O(b), O(1)) and only a direct evaluation is relatively
+    accurate.  F'(a) comes from the trigonometric interpolant of F (modes f):
+    F is smooth, while the direct form -F (rho^2)'(a) / (2 rho^2(a)) divides an
+    O(b^2) dot product of O(b) vectors by rho^2 and loses digits like eps/b.
     """
     near = _near_mask(t_s, a, t, th)
     Y = geo.difference(surface, t_s, a, t, th, near)
@@ -260,7 +264,12 @@ def h3_at_root(surface, t, th, t_s, a, b):
         tau0[near] = geo.tau0_stable(surface, t_s[near], a[near], t[near], th[near])
     rho2 = np.sum(Y * Y, -1)
     F = -np.expm1(-b) / np.sqrt(rho2)
-    dF = -F * np.sum(Y * rth, -1) / rho2
+    if f is None:
+        dF = -F * np.sum(Y * rth, -1) / rho2
+    else:
+        M = (f.shape[-1] - 1) // 2
+        j = np.arange(-M, M + 1)
+        dF = np.real(np.sum(f * (1j * j)[None, :] * np.exp(1j * j[None, :] * a[:, None]), -1))
     dtau0 = np.sum(dnu * Y, -1)
     return tau0 * F ** 3, dtau0 * F ** 3 + 3 * tau0 * F ** 2 * dF
 
@@ -300,8 +309,12 @@ def _tau3_translated(H3, h3, a, b, A, Bn, M, H_a, H1_a):
     n = np.arange(-M, M + 1)
     c = Lb
     out = H_a[:, None] * Bfull[:, n + c]
-    out = out + (H1_a / 2j)[:, None] * (np.exp(-1j * a)[:, None] * Bfull[:, n - 1 + c]
-                                        - np.exp(1j * a)[:, None] * Bfull[:, n + 1 + c])
+    # H3'(a)/(2i) [e^{-ia} B_{n-1}(a,b) - e^{ia} B_{n+1}(a,b)] = H3'(a)/(2i) e^{-ina} (B_{|n-1|} - B_{|n+1|}),
+    # and B_{n-1} - B_{n+1} = <2i sin(th) s^{-3/2}>_n = 2 n e^b A_{|n|} by the identity
+    # d/dth s^{-1/2} = -e^{-b} sin(th) s^{-3/2} (proof of Prop. "lem:Bm"); the difference of two
+    # O(1/b^2) numbers would lose ~log10(1/b^2) digits for small b.
+    phase = np.exp(-1j * n[None, :] * a[:, None])
+    out = out + (H1_a / 2j)[:, None] * phase * (2 * n[None, :] * np.exp(b)[:, None] * A[:, np.abs(n)])
     out = out + swap_convolution(d, a, Btil, M)
     return out
 

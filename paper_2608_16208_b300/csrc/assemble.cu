@@ -68,8 +68,10 @@ __global__ void far_fill_kernel(const FarArgs a) {
 }
 
 // Near fill of one target panel: block per (local target node tl in [0, 16 Mt), delta).
-__global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx scale, const double* __restrict__ coef,
-                                 const cplx* __restrict__ W, cplx* __restrict__ A) {
+// A[row, block] += sS * sum_g coef W_S + sK * sum_g coef W_K   (W_K may be null)
+__global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS, cplx sK,
+                                 const double* __restrict__ coef, const cplx* __restrict__ WS,
+                                 const cplx* __restrict__ WK, cplx* __restrict__ A) {
   const int tl = blockIdx.x;            // l * Mt + i
   const int d = blockIdx.y;
   const int l = tl / Mt, i = tl % Mt;
@@ -77,16 +79,20 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sca
   if (ip < 0 || ip >= Np) return;
   const int64_t tn = (int64_t)jpanel * 16 + l;
   const int64_t row = tn * Mt + i;
-  // W index within the panel chunk: (((l*3 + d)*16 + g)*Mt + i)
-  const cplx* Wg = W + ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
+  // weight index within the panel chunk: (((l*3 + d)*16 + g)*Mt + i)
+  const int64_t base = ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
   const double* cf = coef + ((d * 16 + l) * 16) * 16;   // [g][n]
   cplx* Arow = A + row * N + (int64_t)ip * 16 * Mt;
   for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
     const int n = e / Mt, lp = e % Mt;
-    cplx acc = C(0.0);
+    cplx accS = C(0.0), accK = C(0.0);
 #pragma unroll 4
-    for (int g = 0; g < 16; ++g) acc = acc + cf[g * 16 + n] * Wg[(int64_t)g * Mt * Mt + lp];
-    Arow[e] = Arow[e] + scale * acc;
+    for (int g = 0; g < 16; ++g) {
+      const int64_t w = base + (int64_t)g * Mt * Mt + lp;
+      if (WS) accS = accS + cf[g * 16 + n] * WS[w];
+      if (WK) accK = accK + cf[g * 16 + n] * WK[w];
+    }
+    Arow[e] = Arow[e] + sS * accS + sK * accK;
   }
 }
 
@@ -104,24 +110,27 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
     set_error("bie_assemble_near: bad kernel mask %u", kernels);
     return BIE_EINVAL;
   }
-  if (kernels & BIE_KERNEL_K) { set_error("bie_assemble_near: the double-layer kernel is not in this build"); return BIE_EUNSUPPORTED; }
   const int Mt = s->Mt;
+  const int nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + ((kernels & BIE_KERNEL_K) ? 1 : 0);
   const int64_t chunk_pairs = (int64_t)16 * 48 * Mt;
   cplx* W = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt, ctx->stream);
+  cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt * nk, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(weights)");
   bie_status st = BIE_OK;
-  const cplx scale_s = C(ws_re, ws_im) * (0.5 * s->h);
+  const cplx sS = C(ws_re, ws_im) * (0.5 * s->h), sK = C(wk_re, wk_im) * (0.5 * s->h);
+  const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
+  const cplx* WK = (kernels & BIE_KERNEL_K) ? W + (nk - 1) * chunk_pairs * Mt : nullptr;
   for (int j = 0; j < s->Np && st == BIE_OK; ++j) {
-    PairArgs a = make_pair_args(s, k);
+    PairArgs a = make_pair_args(s, k, kernels);
     a.enumerate = 1;
     a.p0 = (int64_t)j * chunk_pairs;
     a.n_pairs = chunk_pairs;
     a.weights_out = W;
+    a.weights_stride = chunk_pairs * Mt;
     st = launch_pairs(s, a);
     if (st != BIE_OK) break;
     dim3 grid(16 * Mt, 3);
-    near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j, scale_s, s->near_coef, W, (cplx*)A_out);
+    near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j, sS, sK, s->near_coef, WS, WK, (cplx*)A_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");
   }
@@ -142,7 +151,6 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
     case BIE_OP_K_MINUS_I: wk = C(1.0); wid = -1.0; break;
     case BIE_OP_CFIE: wk = C(1.0); wid = 1.0; ws = C(0.0, -eta); break;
   }
-  if (wk.re != 0.0) { set_error("bie_assemble: the double-layer kernel is not in this build"); return BIE_EUNSUPPORTED; }
   FarArgs fa;
   fa.S = s->sp;
   fa.Np = s->Np;

@@ -7,24 +7,30 @@ namespace bie {
 struct PairArgs {
   SurfP S;
   GL16 gl;
-  int Np, Mt, M, P, T, L;
+  int Np, Mt, M, P, T, L;         // P: Toeplitz transform length; L: highest A_m index
+  int kernels;                    // BIE_KERNEL_S | BIE_KERNEL_K
   double h, k;
-  int64_t N, n_pairs, p0;          // p0: first enumerated pair of this launch
-  int enumerate;                 // 1: pair p enumerates every (node, delta, g, theta) of the surface
+  int64_t N, n_pairs, p0;         // p0: first enumerated pair of this launch
+  int enumerate;                  // 1: pair p enumerates every (node, delta, g, theta) of the surface
   const double* t_nodes;
   const double* pts;
   const double* ring_t;
   const double* ring_r;
   const double* ring_n;
   const cplx* tw;
+  const double* rec;              // recurrence coefficient table, 4 doubles per m (see pair_modes.cu)
+  int rec_len;
+  double* scratch;                // per resident warp: (L + 1) x 32 doubles (A), + (L + 1) x 32 (D) if K
+  int64_t scratch_per_warp;       // doubles
   const int64_t* rows;
   const int32_t* srcs;
-  double* modes_out;             // [p][Mt+1] complex, or null
-  cplx* weights_out;             // [p][Mt] complex, or null
+  double* modes_out;              // [p][nk][Mt+1] complex, or null
+  cplx* weights_out;              // [kernel][p][Mt] complex (kernel-major when both), or null
+  int64_t weights_stride;         // complex elements between the S and K weight blocks
   int* status;
 };
 
-PairArgs make_pair_args(bie_surface s, double k);
-bie_status launch_pairs(bie_surface s, const PairArgs& a);
+PairArgs make_pair_args(bie_surface s, double k, unsigned kernels);
+bie_status launch_pairs(bie_surface s, PairArgs& a);
 
 }  // namespace bie

@@ -1,43 +1,123 @@
 // Per-pair pipeline of the correction stage (Sections 3.2-3.4, 4): for a target
 // node x = r(t_j^l, th_i) and a GGQ source ring t_s, the theta_s-Fourier modes
-// of the single-layer kernel e^{ik rho}/rho by singularity swapping, and their
-// Parseval weights on the theta grid.
+// of the single-layer kernel e^{ik rho}/rho (Eq. (Sphi:appr2)) and of the
+// double-layer kernel alpha tau_1 - tau_3 - i beta tau_0 (Eq. (dis:K)) by
+// singularity swapping, and their Parseval weights on the theta grid.
 //
-// One warp per pair.  Steps (all FP64):
-//   1. rho^2 on the ring (Eq. (rho)); samples with |t - t_s| + |th - th_q| <=
-//      kStableDelta use the line integral of the Section 4 Remark, its 16
-//      Gauss-Legendre nodes spread over 16 lanes.
-//   2. a0 = grid argmin refined by real Newton, b0 = sqrt(2 rho^2(a0)/rho^2''(a0)),
-//      complex Newton for theta_+ = a + ib on the analytic continuation
-//      (Section 3.3); roots beyond kBCap are replaced by (a0, kBCap).
-//   3. A_m(b), m = 0..3M (Eq. (Am)): closed-form A_0, A_1 by the AGM, then the
-//      difference recurrence (Eq. (diff-recurrence)) if 3M b <= 7, else
-//      Miller's backward recurrence on the ratios A_{m-1}/A_m.
-//   4. Smooth factors F = (s_{a,b}/rho^2)^{1/2} (Eq. (F-smooth)) and cos(k rho)
-//      packed as one complex FFT of length Mth.
-//   5. Zero-padded FFT convolution (Eq. (convolution) followed by the
-//      <cos k rho> (x) <rho^{-1}> product of Eq. (Sphi:appr2), merged by
-//      associativity): the product of the two trigonometric interpolants is
-//      sampled, shifted by a, on P = 3 Mth points (one inverse FFT), multiplied
-//      by the transform of the circulant A_{|d|}, |d| <= 3M, and transformed
-//      back; modes |m| <= M are exact linear-convolution values.
-//   6. K_m = e^{-ima} y_m + i <sin(k rho)/rho>_m;  Parseval weights
-//      W_l' = (1/Mth) sum'_m K_m e^{i m th_l'}  (Section 3.4).
+// A warp takes a batch of up to 32 pairs:
+//   A. (warp per pair)  rho^2 on the ring, grid minimiser (near-ties to the
+//      sample nearest the target angle, then the lower index).
+//   B. (lane per pair)  real Newton for the minimiser a0, b0 = sqrt(2 rho^2 /
+//      rho^2''), complex Newton for the root theta_+ = a + ib of rho^2
+//      continued to complex theta (Section 3.3); roots beyond kBCap become
+//      (a0, kBCap).  Differences r(t_s, zeta) - r(t, th) near the target are
+//      written in closed form without cancellation (sum-to-product).
+//   C. (lane per pair)  A_m(b), m = 0..L (Eq. (Am)): closed forms A_0, A_1 by
+//      the AGM, then the difference recurrence (Eq. (diff-recurrence)) if
+//      L b <= 7, else Miller's backward recurrence normalised by A_0; written
+//      to the warp's global scratch slice with D_m = A_m - A_{m-1}.
+//   D. (warp per pair)  smooth factors on the grid (F = (s_{a,b}/rho^2)^{1/2},
+//      Eq. (F-smooth); cos(k rho); tau_0 (second-derivative line integral of
+//      the Section 4 Remark near the target), alpha, beta tau_0, H3 = tau_0 F^3),
+//      packed complex FFTs of length Mth, the trigonometric interpolants
+//      multiplied on a grid of P points shifted by a, and the singular
+//      convolutions (Eqs. (convolution), (tau1), (tau3-standard),
+//      (tau3-modified)) as Toeplitz products with the circulants A_{|d|},
+//      B_{|d|} (or B~_{|d|}) through shared-memory FFTs of length P
+//      (P = 3 Mth for S alone, 4 Mth with K).  Modes |m| <= M are exact
+//      linear-convolution values.  Parseval weights: the swapped part through
+//      an inverse FFT (Nyquist split evenly), the smooth part (i sin(k rho)/rho,
+//      -i beta tau_0) by the trapezoid rule (Section 3.2).
 #include <cmath>
+#include <vector>
 
 #include "bie_internal.cuh"
 #include "pair_args.cuh"
 
 namespace bie {
 
-
+constexpr int kMaxWarpsPerBlock = 4;
+constexpr size_t kSmemLimit = 227 * 1024;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// K(m), E(m) by the arithmetic-geometric mean (DLMF 19.8.1, 19.8.6); m1 = 1 - m.
+// ------------------------------------------------------------------ generic trig for real / complex
+__device__ __forceinline__ void trig(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void trig(cplx z, cplx* s, cplx* c) { ccossin(z, c, s); }
+__device__ __forceinline__ double re_of(double v) { return v; }
+__device__ __forceinline__ double re_of(cplx v) { return v.re; }
+__device__ __forceinline__ double shift_by(double v, double s) { return v - s; }
+__device__ __forceinline__ cplx shift_by(cplx v, double s) { return C(v.re - s, v.im); }
+template <typename T>
+__device__ __forceinline__ T mk(double v);
+template <>
+__device__ __forceinline__ double mk<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ cplx mk<cplx>(double v) { return C(v); }
+__device__ __forceinline__ double ipow(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+// r(t_s, ths) - r(t, th) without cancellation (sum-to-product identities); ths real or complex.
+template <typename T>
+__device__ V3<T> diff_ana(const SurfP& S, double ts, T ths, double t, double th) {
+  double s1, c1, s0, c0, smt, cmt;
+  sincos(ts, &s1, &c1);
+  sincos(t, &s0, &c0);
+  sincos(0.5 * (ts + t), &smt, &cmt);
+  const double sdt = sin(0.5 * (ts - t));
+  const double dS = 2 * cmt * sdt;    // sin t_s - sin t
+  const double dC = -2 * smt * sdt;   // cos t_s - cos t
+  const double n2pi = kTwoPi * rint((re_of(ths) - th) / kTwoPi);
+  const T del = shift_by(ths, th + n2pi);        // wrapped th_s - th
+  const T mid = shift_by(0.5 * del, -th);        // th + del/2
+  T sp, cp, sm, cm, sd, cdum;
+  trig(ths, &sp, &cp);
+  trig(mid, &sm, &cm);
+  trig(0.5 * del, &sd, &cdum);
+  const T dCos = -2.0 * (sm * sd);   // cos th_s - cos th
+  const T dSin = 2.0 * (cm * sd);    // sin th_s - sin th
+  if (S.kind == 0) {
+    return {S.ax * (dS * cp + s0 * dCos), S.ay * (dS * sp + s0 * dSin), mk<T>(S.az * dC)};
+  }
+  // star: r = h e;  r_s - r = h_s (e_s - e) + (h_s - h) e
+  const V3<T> de = {dS * cp + s0 * dCos, dS * sp + s0 * dSin, mk<T>(dC)};
+  T hs = mk<T>(1.0), dh = mk<T>(0.0);
+  for (int i = 0; i < S.nt; ++i) {
+    const int p = S.p[i], q = S.q[i];
+    const double mm = S.m[i];
+    double sp_sum = 0.0, cq_sum = 0.0;   // (s1^p - s0^p)/dS and (c1^q - c0^q)/dC
+    for (int j = 0; j < p; ++j) sp_sum += ipow(s1, j) * ipow(s0, p - 1 - j);
+    for (int j = 0; j < q; ++j) cq_sum += ipow(c1, j) * ipow(c0, q - 1 - j);
+    const double g1 = ipow(s1, p) * ipow(c1, q), g0 = ipow(s0, p) * ipow(c0, q);
+    const double dg = dS * sp_sum * ipow(c1, q) + ipow(s0, p) * dC * cq_sum;
+    T smm, cmm, sdm, cdm2, smid, cmid;
+    trig(mm * ths, &smm, &cmm);
+    trig(mm * mid, &smid, &cmid);
+    trig((0.5 * mm) * del, &sdm, &cdm2);
+    T Ts, dT;
+    if (S.s[i] == 0) {
+      Ts = cmm;
+      dT = -2.0 * (smid * sdm);
+    } else {
+      Ts = smm;
+      dT = 2.0 * (cmid * sdm);
+    }
+    hs = hs + (S.c[i] * g1) * Ts;
+    dh = dh + (S.c[i] * dg) * Ts + (S.c[i] * g0) * dT;
+  }
+  double st, ct;
+  sincos(th, &st, &ct);
+  const double ex = s0 * ct, ey = s0 * st, ez = c0;
+  return {hs * de.x + ex * dh, hs * de.y + ey * dh, hs * de.z + ez * dh};
+}
+
+// ------------------------------------------------------------------ AGM (DLMF 19.8.1, 19.8.6)
 __device__ inline void ellipke(double m, double m1, double* K, double* E) {
   double a = 1.0, g = sqrt(m1), c2sum = 0.5 * m, scale = 0.5;
   for (int it = 0; it < 40; ++it) {
@@ -52,8 +132,84 @@ __device__ inline void ellipke(double m, double m1, double* K, double* E) {
   *E = *K * (1.0 - c2sum);
 }
 
-// A_m(b), m = 0..L, sequential (one lane).  Same branches as the CPU restatement.
-__device__ inline void a_modes_seq(double b, int L, double* A, double* D) {
+// ------------------------------------------------------------------ phase B: root (one lane)
+struct PairInfo {
+  int64_t row, ring;
+  double t, th, ts, x, y, z;
+  double a, b, a0;
+  int valid, bi, capped, pad;
+};
+
+__device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, cplx z, cplx* f, cplx* df) {
+  C3 r, rt, rth;
+  surf_eval_c(S, P.ts, z, &r, &rt, &rth);
+  C3 Y;
+  const bool near = fabs(P.ts - P.t) + fabs(wrap_pi(z.re - P.th)) <= kStableDelta;
+  if (near) Y = diff_ana<cplx>(S, P.ts, z, P.t, P.th);
+  else Y = {r.x - C(P.x), r.y - C(P.y), r.z - C(P.z)};
+  *f = Y.x * Y.x + Y.y * Y.y + Y.z * Y.z;
+  *df = 2.0 * (Y.x * rth.x + Y.y * rth.y + Y.z * rth.z);
+}
+
+__device__ inline void locate_root(const SurfP& S, int Mt, PairInfo& P) {
+  const double hgrid = kTwoPi / Mt;
+  double a0 = kTwoPi * P.bi / Mt;
+  const double start = a0;
+  double g0 = 0, g1 = 0, g2 = 0;
+  auto eval_r = [&](double z) {
+    Geo G;
+    surf_eval(S, P.ts, z, 2, &G);
+    const double yx = G.r.x - P.x, yy = G.r.y - P.y, yz = G.r.z - P.z;
+    g0 = yx * yx + yy * yy + yz * yz;
+    g1 = 2 * (yx * G.rth.x + yy * G.rth.y + yz * G.rth.z);
+    g2 = 2 * (dot(G.rth, G.rth) + yx * G.rthth.x + yy * G.rthth.y + yz * G.rthth.z);
+  };
+  for (int it = 0; it < 40; ++it) {
+    eval_r(a0);
+    double step = g2 > 0 ? g1 / g2 : 0.0;
+    step = fmin(fmax(step, -hgrid), hgrid);
+    a0 = fmin(fmax(a0 - step, start - hgrid), start + hgrid);
+    if (fabs(step) <= 1e-15 * (1 + fabs(a0))) break;
+  }
+  eval_r(a0);
+  if (fabs(P.ts - P.t) + fabs(wrap_pi(a0 - P.th)) <= kStableDelta) {   // rho^2(a0) without cancellation
+    const R3 Y = diff_ana<double>(S, P.ts, a0, P.t, P.th);
+    g0 = dot(Y, Y);
+  }
+  const double b0 = sqrt(2 * g0 / (g2 > 0 ? g2 : 0.0));
+  P.a0 = a0;
+  P.capped = !(b0 <= kBCap);
+  cplx z = C(a0, P.capped ? kBCap : b0);
+  bool done = P.capped, extra = false;
+  for (int it = 0; it < 60 && !done; ++it) {
+    cplx f, df;
+    rho2_cplx(S, P, z, &f, &df);
+    const cplx dz = cdiv(f, df);
+    cplx zn = z - dz;
+    if (zn.im < 0) zn = conj(zn);
+    const bool over = !(zn.im <= kBCap);
+    if (over) {
+      P.capped = 1;
+      zn = C(a0, kBCap);
+    }
+    z = zn;
+    const bool small = sqrt(abs2(dz)) <= kRootTol * fabs(z.im) + 4e-16 * sqrt(abs2(z));
+    if (over || extra) done = true;
+    extra = extra || small;
+  }
+  P.a = z.re;
+  P.b = z.im;
+  if (!(P.b > 0.0) || !(P.a == P.a)) {   // no usable root (never expected): fall back to the cap
+    P.a = a0;
+    P.b = kBCap;
+    P.capped = 1;
+  }
+}
+
+// ------------------------------------------------------------------ phase C: A_m, D_m (one lane)
+// rec[4m..4m+3] = (2m-1)/(2m+1), 8m/(2m+1), 4m/(2m-1), (2m+1)/(2m-1)
+__device__ inline void a_modes_lane(double b, int L, const double* __restrict__ rec, int rec_len, double* A,
+                                    double* D, int stride) {
   const double q = exp(-b);
   double K, E;
   ellipke(q * q, -expm1(-2 * b), &K, &E);
@@ -62,343 +218,592 @@ __device__ inline void a_modes_seq(double b, int L, double* A, double* D) {
   if (L * b <= kForwardLimit) {
     double am = A0, dm = (2 / kPi) * ((K - E) / q - K);
     A[0] = am;
-    if (D) D[0] = -dm;
+    D[0] = -dm;
     am += dm;
-    A[1] = am;
-    if (D) D[1] = dm;
+    A[stride] = am;
+    D[stride] = dm;
     for (int m = 1; m < L; ++m) {
-      dm = ((2 * m - 1) * dm + 8 * m * sh2 * am) / (2 * m + 1);
+      dm = rec[4 * m] * dm + (rec[4 * m + 1] * sh2) * am;
       am += dm;
-      A[m + 1] = am;
-      if (D) D[m + 1] = dm;
+      A[(m + 1) * stride] = am;
+      D[(m + 1) * stride] = dm;
     }
     return;
   }
-  // Miller: delta_m = A_{m-1}/A_m - 1 from m = N down to 1 (A_{N+1} = 0), stored for m <= L.
-  const int N = L + (int)ceil(kMillerLog / (2 * b)) + 16;
-  double dn = (2.0 * N + 1 + 8.0 * N * sh2) / (2.0 * N - 1);
-  for (int m = N - 1; m > L; --m) dn = (8 * m * sh2 + (2 * m + 1) * dn / (1 + dn)) / (2 * m - 1);
-  // dn = delta_{L+1}; now the stored range
-  for (int m = L; m >= 1; --m) {
-    dn = (8 * m * sh2 + (2 * m + 1) * dn / (1 + dn)) / (2 * m - 1);
-    A[m] = dn;  // temporarily delta_m
+  // Miller: backward from N with A~_{N+1} = 0, A~_N = 1; rescale on growth; normalise by A_0.
+  int N = L + (int)ceil(kMillerLog / (2 * b)) + 16;
+  if (N > rec_len - 2) N = rec_len - 2;
+  const double ch = cosh(b);
+  double up = 0.0, cur = 1.0;   // A~_{m+1}, A~_m
+  for (int m = N; m >= 1; --m) {
+    const double prev = rec[4 * m + 2] * ch * cur - rec[4 * m + 3] * up;   // A~_{m-1}
+    up = cur;
+    cur = prev;
+    if (m - 1 <= L) A[(m - 1) * stride] = cur;
+    if (fabs(cur) > 1e200) {
+      cur *= 1e-200;
+      up *= 1e-200;
+      for (int j = m - 1; j <= L; ++j) A[j * stride] *= 1e-200;
+    }
   }
-  double am = A0;
-  A[0] = am;
-  for (int m = 1; m <= L; ++m) {
-    const double dl = A[m];
-    const double an = am / (1 + dl);
-    if (D) D[m] = -an * dl;
-    am = an;
-    A[m] = am;
+  const double f = A0 / A[0];
+  double prevA = 0.0;
+  for (int m = 0; m <= L; ++m) {
+    const double am = A[m * stride] * f;
+    A[m * stride] = am;
+    if (m) D[m * stride] = am - prevA;
+    prevA = am;
   }
-  if (D) D[0] = -D[1];
+  D[0] = A[0] - A[stride];
 }
 
-struct RootOut {
-  double a, b, a0, b0;
-  int capped;
+// ------------------------------------------------------------------ small helpers of phase D
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// sin(k x) - k sin(x), k >= 0, without cancellation (series when k x < 1).
+__device__ inline double sin_k_minus(int k, double x) {
+  const double kx = k * x;
+  if (fabs(kx) < 1.0) {
+    const double kx2 = kx * kx, x2 = x * x;
+    double an = kx * kx2 / 6.0, bn = k * x * x2 / 6.0, acc = 0.0, sg = -1.0;
+    for (int n = 1; n <= 12; ++n) {
+      acc += sg * (an - bn);
+      const double den = (2.0 * n + 2) * (2.0 * n + 3);
+      an *= kx2 / den;
+      bn *= x2 / den;
+      sg = -sg;
+    }
+    return acc;
+  }
+  return sin(kx) - k * sin(x);
+}
+
+struct Smem {
+  double *rho2, *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal, *VK, *VH, *Atab, *Dtab, *Btab;
+  cplx *W0, *W1, *ph, *kc, *kk;
+  PairInfo* info;
 };
 
-// rho^2 and derivatives at real theta_s = z (warp-cooperative; identical on all lanes).
-__device__ inline void eval_real(const PairArgs& a, double ts, double t, double th, const R3& x, double z, double* g0,
-                                 double* g1, double* g2) {
+__host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK) {
+  const int M = Mt / 2;
+  size_t d = 0;
+  d += 2 * Mt;                               // rho2, sn
+  d += withK ? 4 * Mt : 0;                   // tau0, bt0, hr, alph
+  d += P;                                    // Acal
+  d += withK ? 3 * P : 0;                    // Bcal, VK, VH
+  d += (L + 1);                              // Atab
+  d += withK ? 2 * (L + 1) : 0;              // Dtab, Btab
+  d += 4 * P;                                // W0, W1 (complex)
+  d += 2 * (withK ? 3 : 2) * (2 * M + 1);    // ph, kc (, kk)
+  d += 32 * (sizeof(PairInfo) / 8);          // batch info
+  return d;
+}
+
+__device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
+  const int M = Mt / 2;
+  Smem s = {};
+  double* p = base;
+  s.rho2 = p; p += Mt;
+  s.sn = p; p += Mt;
+  if (withK) { s.tau0 = p; p += Mt; s.bt0 = p; p += Mt; s.hr = p; p += Mt; s.alph = p; p += Mt; }
+  s.Acal = p; p += P;
+  if (withK) { s.Bcal = p; p += P; s.VK = p; p += P; s.VH = p; p += P; }
+  s.Atab = p; p += L + 1;
+  if (withK) { s.Dtab = p; p += L + 1; s.Btab = p; p += L + 1; }
+  s.W0 = (cplx*)p; p += 2 * P;
+  s.W1 = (cplx*)p; p += 2 * P;
+  s.ph = (cplx*)p; p += 2 * (2 * M + 1);
+  s.kc = (cplx*)p; p += 2 * (2 * M + 1);
+  if (withK) { s.kk = (cplx*)p; p += 2 * (2 * M + 1); }
+  s.info = (PairInfo*)p;
+  return s;
+}
+
+// e^{ija} Z_j / Mt (j = -M..M, Nyquist split evenly) placed on the P grid in X, inverse
+// transform with scratch Y; returns the buffer holding the result.
+__device__ inline cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y, int Mt, int P, const cplx* tw,
+                                 int T) {
   const int lane = threadIdx.x & 31;
-  Geo G;
-  surf_eval(a.S, ts, z, 2, &G);
-  R3 Y = {G.r.x - x.x, G.r.y - x.y, G.r.z - x.z};
-  const double dt = t - ts;
-  const double dth = wrap_pi(th - z);
-  const bool near = fabs(dt) + fabs(dth) <= kStableDelta;
-  if (near) {
-    double cx = 0, cy = 0, cz = 0;
-    if (lane < 16) {
-      Geo P;
-      surf_eval(a.S, ts + a.gl.x[lane] * dt, z + a.gl.x[lane] * dth, 1, &P);
-      const double w = a.gl.w[lane];
-      cx = w * (dt * P.rt.x + dth * P.rth.x);
-      cy = w * (dt * P.rt.y + dth * P.rth.y);
-      cz = w * (dt * P.rt.z + dth * P.rth.z);
-    }
-    Y = {-warp_sum(cx), -warp_sum(cy), -warp_sum(cz)};
+  const int M = Mt / 2;
+  for (int pp = lane; pp < P; pp += 32) X[pp] = C(0.0);
+  __syncwarp();
+  for (int jj = lane; jj <= 2 * M; jj += 32) {
+    const int jv = jj - M;
+    cplx z = Z[wrapi(jv, Mt)] * (1.0 / Mt);
+    if (jv == M || jv == -M) z = 0.5 * z;
+    X[wrapi(jv, P)] = ph[jj] * z;
   }
-  *g0 = dot(Y, Y);
-  *g1 = 2 * dot(Y, G.rth);
-  *g2 = 2 * (dot(G.rth, G.rth) + dot(Y, G.rthth));
+  __syncwarp();
+  return warp_fft(X, Y, P, tw, T, +1);
 }
 
-// rho^2(zeta) and its derivative for complex zeta (warp-cooperative).
-__device__ inline void eval_cplx(const PairArgs& a, double ts, double t, double th, const R3& x, cplx z, cplx* P,
-                                 cplx* dP) {
-  const int lane = threadIdx.x & 31;
-  C3 r, rt, rth;
-  surf_eval_c(a.S, ts, z, &r, &rt, &rth);
-  C3 Y = {r.x - C(x.x), r.y - C(x.y), r.z - C(x.z)};
-  const double dt = t - ts;
-  const cplx dth = C(wrap_pi(th - z.re), -z.im);
-  const bool near = fabs(dt) + fabs(dth.re) <= kStableDelta;
-  if (near) {
-    cplx cx = C(0), cy = C(0), cz = C(0);
-    if (lane < 16) {
-      C3 pr, prt, prth;
-      surf_eval_c(a.S, ts + a.gl.x[lane] * dt, z + a.gl.x[lane] * dth, &pr, &prt, &prth);
-      const double w = a.gl.w[lane];
-      cx = w * (dt * prt.x + prth.x * dth);
-      cy = w * (dt * prt.y + prth.y * dth);
-      cz = w * (dt * prt.z + prth.z * dth);
-    }
-    Y = {C(-warp_sum(cx.re), -warp_sum(cx.im)), C(-warp_sum(cy.re), -warp_sum(cy.im)),
-         C(-warp_sum(cz.re), -warp_sum(cz.im))};
-  }
-  *P = Y.x * Y.x + Y.y * Y.y + Y.z * Y.z;
-  *dP = 2.0 * (Y.x * rth.x + Y.y * rth.y + Y.z * rth.z);
-}
-
-__device__ inline RootOut locate_root(const PairArgs& a, double ts, double t, double th, const R3& x, double a0) {
-  const double hgrid = kTwoPi / a.Mt;
-  const double start = a0;
-  double g0, g1, g2;
-  for (int it = 0; it < 40; ++it) {
-    eval_real(a, ts, t, th, x, a0, &g0, &g1, &g2);
-    double step = g2 > 0 ? g1 / g2 : 0.0;
-    step = fmin(fmax(step, -hgrid), hgrid);
-    a0 = fmin(fmax(a0 - step, start - hgrid), start + hgrid);
-    if (fabs(step) <= 1e-15 * (1 + fabs(a0))) break;
-  }
-  eval_real(a, ts, t, th, x, a0, &g0, &g1, &g2);
-  const double b0 = sqrt(2 * g0 / (g2 > 0 ? g2 : 0.0));
-  RootOut o;
-  o.a0 = a0;
-  o.b0 = b0;
-  o.capped = !(b0 <= kBCap);
-  cplx z = C(a0, o.capped ? kBCap : b0);
-  bool done = o.capped, extra = false;
-  for (int it = 0; it < 60 && !done; ++it) {
-    cplx P, dP;
-    eval_cplx(a, ts, t, th, x, z, &P, &dP);
-    const cplx dz = cdiv(P, dP);
-    cplx zn = z - dz;
-    if (zn.im < 0) zn = conj(zn);
-    const bool over = !(zn.im <= kBCap);
-    if (over) {
-      o.capped = 1;
-      zn = C(a0, kBCap);
-    }
-    z = zn;
-    const bool small = sqrt(abs2(dz)) <= kRootTol * fabs(z.im) + 4e-16 * sqrt(abs2(z));
-    if (over || extra) done = true;
-    extra = extra || small;
-  }
-  o.a = z.re;
-  o.b = z.im;
-  return o;
-}
-
-__global__ void __launch_bounds__(128) pair_s_kernel(const PairArgs a) {
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const PairArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
-  // per-warp shared memory (doubles): 6 Mt + 5 P + L + 5
-  const int per_warp = 6 * Mt + 5 * P + L + 5;
-  double* base = smem + (size_t)wib * per_warp;
-  double* rho2 = base;                      // Mt
-  double* sn = rho2 + Mt;                   // Mt
-  double* Acal = sn + Mt;                   // P: transform of the circulant A_{|d|}
-  cplx* bufA = (cplx*)(Acal + P);           // P
-  cplx* bufB = bufA + P;                    // P
-  double* Atab = (double*)(bufB + P);       // L + 1
-  cplx* ph = (cplx*)(Atab + L + 1);         // 2M + 1: e^{i j a}, j = -M..M
-  cplx* kc = ph + 2 * M + 1;                // 2M + 1: Kc_m, m = -M..M
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const bool wantS = a.kernels & BIE_KERNEL_S, wantK = a.kernels & BIE_KERNEL_K;
+  const size_t per_warp = smem_doubles(Mt, P, L, wantK);
+  Smem sm = carve(smem + per_warp * wib, Mt, P, L, wantK);
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = warp; p < a.n_pairs; p += nwarps) {
-    // ---- decode the pair
-    int64_t row;
-    int d, g;
-    if (a.enumerate) {
-      const int64_t pg = a.p0 + p;
-      const int i = (int)(pg % Mt);
-      int64_t rest = pg / Mt;
-      g = (int)(rest % 16);
-      rest /= 16;
-      d = (int)(rest % 3);
-      row = (rest / 3) * Mt + i;
-    } else {
-      row = a.rows[p];
-      const int src = a.srcs[p];
-      d = src / 16;
-      g = src % 16;
-      if (src < 0 || src >= 48) d = -1;
-    }
-    const int64_t tn = row / Mt;
-    const int i = (int)(row % Mt);
-    const int j = (int)(tn / 16);
-    const int ip = j + d - 1;
-    if (row < 0 || row >= a.N || d < 0 || ip < 0 || ip >= a.Np) {
-      if (a.modes_out)
-        for (int m = lane; m < 2 * (Mt + 1); m += 32) a.modes_out[p * 2 * (Mt + 1) + m] = 0.0;
-      if (a.weights_out)
-        for (int m = lane; m < Mt; m += 32) a.weights_out[p * Mt + m] = C(0.0);
-      if (!a.enumerate && lane == 0) atomicAdd(a.status, 1);
-      continue;
-    }
-    const int64_t ring = (tn * 3 + d) * 16 + g;
-    const double t = a.t_nodes[tn];
-    const double th = kTwoPi * i / Mt;
-    const double ts = a.ring_t[ring];
-    const R3 x = {a.pts[3 * row], a.pts[3 * row + 1], a.pts[3 * row + 2]};
-    const double* rr = a.ring_r + ring * 3 * Mt;
-    const double dts = fabs(t - ts);
-    // ---- 1. rho^2 on the ring (direct), then the near samples by the line integral
-    for (int q = lane; q < Mt; q += 32) {
-      const double yx = rr[3 * q] - x.x, yy = rr[3 * q + 1] - x.y, yz = rr[3 * q + 2] - x.z;
-      rho2[q] = yx * yx + yy * yy + yz * yz;
+  double* scrA = a.scratch + gwarp * a.scratch_per_warp;
+  double* scrD = scrA + (int64_t)(L + 1) * 32;
+  const int nk = (wantS ? 1 : 0) + (wantK ? 1 : 0);
+
+  for (int64_t p0 = gwarp * 32; p0 < a.n_pairs; p0 += nwarps * 32) {
+    const int nb = (int)min((int64_t)32, a.n_pairs - p0);
+    // ---------------- decode the batch (lane per pair)
+    if (lane < nb) {
+      const int64_t p = p0 + lane;
+      int64_t row;
+      int d, g;
+      if (a.enumerate) {
+        const int64_t pg = a.p0 + p;
+        const int i = (int)(pg % Mt);
+        int64_t rest = pg / Mt;
+        g = (int)(rest % 16);
+        rest /= 16;
+        d = (int)(rest % 3);
+        row = (rest / 3) * Mt + i;
+      } else {
+        row = a.rows[p];
+        const int src = a.srcs[p];
+        d = src / 16;
+        g = src % 16;
+        if (src < 0 || src >= 48) d = -1;
+      }
+      PairInfo pr = {};
+      const int64_t tn = row / Mt;
+      const int ip = (int)(tn / 16) + d - 1;
+      pr.valid = !(row < 0 || row >= a.N || d < 0 || ip < 0 || ip >= a.Np);
+      pr.row = row;
+      if (pr.valid) {
+        pr.ring = (tn * 3 + d) * 16 + g;
+        pr.t = a.t_nodes[tn];
+        pr.th = kTwoPi * (int)(row % Mt) / Mt;
+        pr.ts = a.ring_t[pr.ring];
+        pr.x = a.pts[3 * row];
+        pr.y = a.pts[3 * row + 1];
+        pr.z = a.pts[3 * row + 2];
+      } else if (!a.enumerate) {
+        atomicAdd(a.status, 1);
+      }
+      sm.info[lane] = pr;
     }
     __syncwarp();
-    {
-      const int K = (int)ceil(kStableDelta * Mt / kTwoPi) + 1;
-      for (int c0 = -K; c0 <= K; c0 += 2) {
-        const int c = c0 + (lane >> 4);
-        const int q = ((i + c) % Mt + Mt) % Mt;
+    // ---------------- A. grid minimiser (warp per pair)
+    for (int pi = 0; pi < nb; ++pi) {
+      const PairInfo pr = sm.info[pi];
+      if (!pr.valid) continue;
+      const double* rr = a.ring_r + pr.ring * 3 * Mt;
+      const int i = (int)(pr.row % Mt);
+      const double dts = fabs(pr.t - pr.ts);
+      double bv = INFINITY;
+      for (int q = lane; q < Mt; q += 32) {
         const double thq = kTwoPi * q / Mt;
-        const double dth = wrap_pi(th - thq);
-        const bool nearq = (c <= K) && (dts + fabs(dth) <= kStableDelta);
-        if (!__ballot_sync(0xffffffffu, nearq)) continue;
-        double cx = 0, cy = 0, cz = 0;
-        if (nearq) {
-          const int jn = lane & 15;
+        double r2;
+        if (dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta) {
+          const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
+          r2 = dot(Y, Y);
+        } else {
+          const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
+          r2 = yx * yx + yy * yy + yz * yz;
+        }
+        sm.rho2[q] = r2;
+        bv = fmin(bv, r2);
+      }
+      for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+      __syncwarp();
+      int bkey = 0x7fffffff;
+      for (int q = lane; q < Mt; q += 32)
+        if (sm.rho2[q] <= bv * (1 + 1e-12)) {
+          const int dq = q > i ? q - i : i - q;
+          bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
+        }
+      for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
+      if (lane == 0) sm.info[pi].bi = bkey % Mt;
+      __syncwarp();
+    }
+    // ---------------- B. complex root and C. A_m, D_m (lane per pair)
+    if (lane < nb && sm.info[lane].valid) {
+      PairInfo pr = sm.info[lane];
+      locate_root(a.S, Mt, pr);
+      sm.info[lane].a = pr.a;
+      sm.info[lane].b = pr.b;
+      sm.info[lane].a0 = pr.a0;
+      sm.info[lane].capped = pr.capped;
+      a_modes_lane(pr.b, L, a.rec, a.rec_len, scrA + lane, scrD + lane, 32);
+    }
+    __syncwarp();
+    // ---------------- D. per pair (warp)
+    for (int pi = 0; pi < nb; ++pi) {
+      const PairInfo pr = sm.info[pi];
+      const int64_t p = p0 + pi;
+      if (!pr.valid) {
+        if (a.modes_out)
+          for (int m = lane; m < 2 * nk * (Mt + 1); m += 32) a.modes_out[p * 2 * nk * (Mt + 1) + m] = 0.0;
+        if (a.weights_out)
+          for (int kk = 0; kk < nk; ++kk)
+            for (int m = lane; m < Mt; m += 32) a.weights_out[kk * a.weights_stride + p * Mt + m] = C(0.0);
+        continue;
+      }
+      const double ra = pr.a, rb = pr.b;
+      const double* rr = a.ring_r + pr.ring * 3 * Mt;
+      const double* rn = a.ring_n + pr.ring * 3 * Mt;
+      const double dts = fabs(pr.t - pr.ts);
+      const double qb = exp(-rb), om = -expm1(-rb);
+      const bool translated = wantK && rb < kSmallB;
+      // ---- D1. A_m (and D_m, B_m) of this pair; phases e^{ija}
+      for (int m = lane; m <= L; m += 32) {
+        sm.Atab[m] = scrA[m * 32 + pi];
+        if (wantK) sm.Dtab[m] = scrD[m * 32 + pi];
+      }
+      for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
+      __syncwarp();
+      if (wantK) {  // B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b, m = 0..2M+1
+        const double shb = sinh(rb), sh2b = sinh(0.5 * rb) * sinh(0.5 * rb);
+        const double fac = exp(rb) / (shb * shb);
+        for (int m = lane; m <= 2 * M + 1; m += 32)
+          sm.Btab[m] = -(m - 0.5) * fac * (sm.Dtab[m] + 2 * sh2b * sm.Atab[m]);
+        __syncwarp();
+      }
+      // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and, with K, B_{|d|} or B~_{|d|} (|d| <= 2M)
+      for (int pp = lane; pp < P; pp += 32) {
+        const int dd = pp <= P / 2 ? pp : P - pp;
+        const double av = dd <= L ? sm.Atab[dd] : 0.0;
+        double bv = 0.0;
+        if (wantK && dd <= 2 * M) {
+          bv = sm.Btab[dd];
+          if (translated) bv = (sm.Atab[dd] - om * om * bv) / (4 * qb);
+        }
+        sm.W1[pp] = C(av, bv);
+      }
+      __syncwarp();
+      {
+        const cplx* Af = warp_fft(sm.W1, sm.W0, P, a.tw, a.T, -1);
+        for (int pp = lane; pp < P; pp += 32) {
+          sm.Acal[pp] = Af[pp].re;
+          if (wantK) sm.Bcal[pp] = Af[pp].im;
+        }
+      }
+      __syncwarp();
+      // ---- D3. samples
+      for (int q = lane; q < Mt; q += 32) {
+        const double thq = kTwoPi * q / Mt;
+        const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta;
+        double yx, yy, yz;
+        if (near) {
+          const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
+          yx = Y.x; yy = Y.y; yz = Y.z;
+        } else {
+          yx = rr[3 * q] - pr.x; yy = rr[3 * q + 1] - pr.y; yz = rr[3 * q + 2] - pr.z;
+        }
+        const double r2 = yx * yx + yy * yy + yz * yz;
+        const double rho = sqrt(r2);
+        const double sp = sin(0.5 * (thq - ra));
+        const double s = om * om + 4 * qb * sp * sp;
+        const double F = sqrt(s / r2);
+        double skr, ckr;
+        sincos(a.k * rho, &skr, &ckr);
+        sm.rho2[q] = r2;
+        sm.W0[q] = C(F, ckr);          // F + i cos(k rho)
+        sm.sn[q] = skr / rho;
+        if (wantK) {
+          const double x = a.k * rho;
+          double al, be;
+          if (x < kSeriesX) {  // Taylor series of alpha/k^2 and beta/k^3
+            const double x2 = x * x;
+            double sa = 0.0, sb = 0.0, pw = 1.0, fa = 2.0, fb = 6.0;
+            for (int n = 1; n <= 9; ++n) {
+              const double sg = (n & 1) ? 1.0 : -1.0;
+              sa += sg * (1 - 2 * n) / fa * pw;
+              sb += sg * (2 * n) / fb * pw;
+              pw *= x2;
+              fa *= (2 * n + 1) * (2 * n + 2);
+              fb *= (2 * n + 2) * (2 * n + 3);
+            }
+            al = a.k * a.k * sa;
+            be = a.k * a.k * a.k * sb;
+          } else {
+            al = (1 - ckr - x * skr) / r2;
+            be = (skr - x * ckr) / (r2 * rho);
+          }
+          sm.tau0[q] = rn[3 * q] * yx + rn[3 * q + 1] * yy + rn[3 * q + 2] * yz;   // near ones replaced below
+          sm.alph[q] = al;
+          sm.bt0[q] = be;
+          sm.hr[q] = F;
+        }
+      }
+      __syncwarp();
+      if (wantK) {
+        // tau_0 of near samples: second-derivative line integral (Section 4 Remark), 16 lanes per sample
+        const int i = (int)(pr.row % Mt);
+        const int Kw = (int)ceil(kStableDelta * Mt / kTwoPi) + 1;
+        for (int c0 = -Kw; c0 <= Kw; c0 += 2) {
+          const int c = c0 + (lane >> 4);
+          const int q = wrapi(i + c, Mt);
+          const double thq = kTwoPi * q / Mt;
+          const double dth = wrap_pi(pr.th - thq);
+          const bool nearq = (c <= Kw) && (dts + fabs(dth) <= kStableDelta);
+          if (!__ballot_sync(0xffffffffu, nearq)) continue;
+          double acc = 0.0;
+          if (nearq) {
+            const int jn = lane & 15;
+            const double dt = pr.t - pr.ts, lam = a.gl.x[jn];
+            Geo G;
+            surf_eval(a.S, pr.ts + lam * dt, thq + lam * dth, 2, &G);
+            const double qx = G.rtt.x * dt * dt + 2 * G.rtth.x * dt * dth + G.rthth.x * dth * dth;
+            const double qy = G.rtt.y * dt * dt + 2 * G.rtth.y * dt * dth + G.rthth.y * dth * dth;
+            const double qz = G.rtt.z * dt * dt + 2 * G.rtth.z * dt * dth + G.rthth.z * dth * dth;
+            acc = a.gl.w[jn] * (lam - 1) * (rn[3 * q] * qx + rn[3 * q + 1] * qy + rn[3 * q + 2] * qz);
+          }
+          for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (nearq && (lane & 15) == 0) sm.tau0[q] = acc;
+          __syncwarp();
+        }
+        __syncwarp();
+        for (int q = lane; q < Mt; q += 32) {
+          const double F = sm.hr[q], t0 = sm.tau0[q];
+          sm.bt0[q] *= t0;              // beta tau_0
+          sm.hr[q] = t0 * F * F * F;    // H3 = tau_0 F^3
+        }
+        __syncwarp();
+      }
+      // ---- D4. S: FFT of F + i cos(k rho), upsample, Toeplitz with A
+      cplx* Z1 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+      cplx* Zf = (Z1 == sm.W0) ? sm.W1 : sm.W0;
+      double dFa = 0.0;   // F'(a) from the interpolant of F (well conditioned, unlike the direct form)
+      if (translated) {
+        double acc = 0.0;
+        for (int jj = lane; jj <= 2 * M; jj += 32) {
+          const int jv = jj - M;
+          const cplx zp = Z1[wrapi(jv, Mt)], zm = conj(Z1[wrapi(-jv, Mt)]);
+          cplx fj = 0.5 * (zp + zm) * (1.0 / Mt);
+          if (jv == M || jv == -M) fj = 0.5 * fj;
+          const cplx v = fj * sm.ph[jj];
+          acc += -jv * v.im;   // Re(f_j i j e^{ija})
+        }
+        dFa = warp_sum(acc);
+      }
+      cplx* up1 = upsample(Z1, sm.ph, Zf, Z1, Mt, P, a.tw, a.T);   // re: F~, im: C~
+      cplx* uf = (up1 == sm.W0) ? sm.W1 : sm.W0;
+      if (wantK)
+        for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up1[pp].re;   // keep F~ for V_K
+      if (wantS) {
+        for (int pp = lane; pp < P; pp += 32) uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], 0.0);
+        __syncwarp();
+        const cplx* Yf = warp_fft(uf, up1, P, a.tw, a.T, -1);
+        for (int jj = lane; jj <= 2 * M; jj += 32) sm.kc[jj] = conj(sm.ph[jj]) * Yf[wrapi(jj - M, P)] * (1.0 / P);
+      }
+      __syncwarp();
+      if (wantK) {
+        // ---- D5. V_K = alpha~ tau0~ F~ on the P grid
+        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], sm.alph[q]);
+        __syncwarp();
+        cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+        cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
+        cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.T);   // re: tau0~, im: alpha~
+        for (int pp = lane; pp < P; pp += 32) sm.VK[pp] = up2[pp].re * up2[pp].im * sm.VH[pp];
+        __syncwarp();
+        // ---- D6. H3 modes (symmetric), with beta tau_0 packed in the imaginary part
+        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.hr[q], sm.bt0[q]);
+        __syncwarp();
+        const cplx* Z3 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+        for (int jj = lane; jj <= 2 * M; jj += 32) {
+          const int jv = jj - M;
+          const cplx zp = Z3[wrapi(jv, Mt)], zm = conj(Z3[wrapi(-jv, Mt)]);
+          cplx h = 0.5 * (zp + zm) * (1.0 / Mt);
+          if (jv == M || jv == -M) h = 0.5 * h;
+          sm.kk[jj] = h;
+        }
+        __syncwarp();
+        double H3a = 0.0, H3pa = 0.0;
+        if (translated) {
+          // ---- D7. H3(a), H3'(a) directly from the geometry at th_s = a
+          const bool neara = dts + fabs(wrap_pi(ra - pr.th)) <= kStableDelta;
+          R3 Y;
           Geo G;
-          const double dt = t - ts;
-          surf_eval(a.S, ts + a.gl.x[jn] * dt, thq + a.gl.x[jn] * dth, 1, &G);
-          const double w = a.gl.w[jn];
-          cx = w * (dt * G.rt.x + dth * G.rth.x);
-          cy = w * (dt * G.rt.y + dth * G.rth.y);
-          cz = w * (dt * G.rt.z + dth * G.rth.z);
+          surf_eval(a.S, pr.ts, ra, 2, &G);
+          if (neara) Y = diff_ana<double>(a.S, pr.ts, ra, pr.t, pr.th);
+          else Y = {G.r.x - pr.x, G.r.y - pr.y, G.r.z - pr.z};
+          const R3 n = cross(G.rt, G.rth);
+          const double J = sqrt(dot(n, n));
+          const R3 nu = {n.x / J, n.y / J, n.z / J};
+          const R3 dn1 = cross(G.rtth, G.rth), dn2 = cross(G.rt, G.rthth);
+          const R3 dn = {dn1.x + dn2.x, dn1.y + dn2.y, dn1.z + dn2.z};
+          const double nd = dot(nu, dn);
+          const R3 dnu = {(dn.x - nu.x * nd) / J, (dn.y - nu.y * nd) / J, (dn.z - nu.z * nd) / J};
+          double t0a = dot(nu, Y);
+          if (neara) {
+            double acc = 0.0;
+            if (lane < 16) {
+              const double dt = pr.t - pr.ts, dth = wrap_pi(pr.th - ra), lam = a.gl.x[lane];
+              Geo H;
+              surf_eval(a.S, pr.ts + lam * dt, ra + lam * dth, 2, &H);
+              const double qx = H.rtt.x * dt * dt + 2 * H.rtth.x * dt * dth + H.rthth.x * dth * dth;
+              const double qy = H.rtt.y * dt * dt + 2 * H.rtth.y * dt * dth + H.rthth.y * dth * dth;
+              const double qz = H.rtt.z * dt * dt + 2 * H.rtth.z * dt * dth + H.rthth.z * dth * dth;
+              acc = a.gl.w[lane] * (lam - 1) * (nu.x * qx + nu.y * qy + nu.z * qz);
+            }
+            t0a = warp_sum(acc);
+          }
+          const double r2a = dot(Y, Y);
+          const double Fa = om / sqrt(r2a);
+          const double dt0 = dot(dnu, Y);
+          H3a = t0a * Fa * Fa * Fa;
+          H3pa = dt0 * Fa * Fa * Fa + 3 * t0a * Fa * Fa * dFa;
+          // ---- D8. remainder R on the grid (stable sum within kNearPhi of a); modes d_k
+          for (int q = lane; q < Mt; q += 32) {
+            const double phq = wrap_pi(kTwoPi * q / Mt - ra);
+            const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
+            sm.tau0[q] = (fabs(phq) < kNearPhi) ? 0.0 : (sm.hr[q] - H3a - H3pa * sin(phq)) / s2;
+          }
+          __syncwarp();
+          for (int q = 0; q < Mt; ++q) {
+            const double phq = wrap_pi(kTwoPi * q / Mt - ra);
+            if (!(fabs(phq) < kNearPhi)) continue;
+            const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
+            double acc = 0.0;
+            for (int jj = lane; jj <= 2 * M; jj += 32) {
+              const int kv = jj - M, ka = kv < 0 ? -kv : kv;
+              const cplx hv = sm.kk[jj] * sm.ph[jj];   // h3_k e^{ika}
+              double gre, gim;
+              if (s2 == 0.0) {
+                gre = -2.0 * ka * ka;
+                gim = 0.0;
+              } else {
+                const double sk = sin(0.5 * ka * phq);
+                gre = -2.0 * sk * sk / s2;
+                gim = (kv < 0 ? -1.0 : 1.0) * sin_k_minus(ka, phq) / s2;
+              }
+              acc += hv.re * gre - hv.im * gim;
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) sm.tau0[q] = acc;
+            __syncwarp();
+          }
+          __syncwarp();
+          for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], 0.0);
+          __syncwarp();
+          const cplx* Zr = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+          for (int jj = lane; jj <= 2 * M; jj += 32) {
+            const int jv = jj - M;
+            cplx dv = Zr[wrapi(jv, Mt)] * (1.0 / Mt);
+            if (jv == M || jv == -M) dv = 0.5 * dv;
+            sm.kk[jj] = dv;        // kk now holds d_k
+          }
+          __syncwarp();
         }
-        for (int o = 8; o; o >>= 1) {
-          cx += __shfl_xor_sync(0xffffffffu, cx, o);
-          cy += __shfl_xor_sync(0xffffffffu, cy, o);
-          cz += __shfl_xor_sync(0xffffffffu, cz, o);
+        // ---- D9. upsample h3 (or d), multiply by the B (or B~) transform
+        {
+          for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(0.0);
+          __syncwarp();
+          for (int jj = lane; jj <= 2 * M; jj += 32) sm.W0[wrapi(jj - M, P)] = sm.ph[jj] * sm.kk[jj];
+          __syncwarp();
+          const cplx* up3 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, +1);
+          for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up3[pp].re * sm.Bcal[pp];
+          __syncwarp();
         }
-        if (nearq && (lane & 15) == 0) rho2[q] = cx * cx + cy * cy + cz * cz;
+        // ---- D10. transform (V_K Acal) + i (V_H), unpack AT1 and the tau_3 Toeplitz part
+        for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(sm.VK[pp] * sm.Acal[pp], sm.VH[pp]);
+        __syncwarp();
+        const cplx* Y2 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, -1);
+        for (int jj = lane; jj <= 2 * M; jj += 32) {
+          const int m = jj - M;
+          const cplx zp = Y2[wrapi(m, P)], zm = conj(Y2[wrapi(-m, P)]);
+          const cplx y1 = 0.5 * (zp + zm) * (1.0 / P);
+          const cplx y2 = C(0.5 * (zp.im - zm.im), -0.5 * (zp.re - zm.re)) * (1.0 / P);
+          const cplx e = conj(sm.ph[jj]);                                  // e^{-ima}
+          cplx t3 = e * y2;
+          if (translated) {
+            // H3(a) B_n(a,b) + H3'(a)/(2i) e^{-ina} (B_{|n-1|} - B_{|n+1|}), with the exact
+            // cancellation-free B_{n-1} - B_{n+1} = 2 n e^b A_{|n|}
+            const int ma = m < 0 ? -m : m;
+            const cplx expl = C(H3a * sm.Btab[ma], -H3pa * m * exp(rb) * sm.Atab[ma]);
+            t3 = t3 + e * expl;
+          }
+          sm.kk[jj] = e * y1 - t3;   // swapped part of K (kk was consumed in D9)
+        }
+        __syncwarp();
       }
-    }
-    __syncwarp();
-    // grid minimiser; near-ties (within 1e-12) go to the sample nearest the target angle
-    // (integer grid distance), then to the lower index
-    double bv = INFINITY;
-    for (int q = lane; q < Mt; q += 32) bv = fmin(bv, rho2[q]);
-    for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
-    int bkey = 0x7fffffff;
-    for (int q = lane; q < Mt; q += 32) {
-      if (rho2[q] <= bv * (1 + 1e-12)) {
-        const int dq = q > i ? q - i : i - q;
-        const int key = min(dq, Mt - dq) * Mt + q;
-        bkey = min(bkey, key);
-      }
-    }
-    for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
-    const int bi = bkey % Mt;
-    // ---- 2. complex root
-    const RootOut ro = locate_root(a, ts, t, th, x, kTwoPi * bi / Mt);
-    const double ra = ro.a, rb = ro.b;
-    // ---- 3. A_m(b), m = 0..L, and the transform of the circulant A_{|d|}, |d| <= 3M
-    if (lane == 0) a_modes_seq(rb, L, Atab, nullptr);
-    __syncwarp();
-    for (int pp = lane; pp < P; pp += 32) {
-      const int dd = pp <= P / 2 ? pp : P - pp;
-      bufA[pp] = C(dd <= 3 * M ? Atab[dd] : 0.0, 0.0);
-    }
-    __syncwarp();
-    {
-      const cplx* Af = warp_fft(bufA, bufB, P, a.tw, a.T, -1);
-      for (int pp = lane; pp < P; pp += 32) Acal[pp] = Af[pp].re;
-    }
-    for (int jj = lane; jj <= 2 * M; jj += 32) ph[jj] = cexpi((jj - M) * ra);
-    // ---- 4. smooth factors, packed: F + i cos(k rho)
-    const double qb = exp(-rb), om = -expm1(-rb);
-    for (int q = lane; q < Mt; q += 32) {
-      const double phi = kTwoPi * q / Mt - ra;
-      const double sp = sin(phi / 2);
-      const double s = om * om + 4 * qb * sp * sp;
-      const double r2 = rho2[q];
-      const double rho = sqrt(r2);
-      double skr, ckr;
-      sincos(a.k * rho, &skr, &ckr);
-      bufA[q] = C(sqrt(s / r2), ckr);
-      sn[q] = skr / rho;
-    }
-    __syncwarp();
-    cplx* Z = warp_fft(bufA, bufB, Mt, a.tw, a.T, -1);
-    cplx* Xb = (Z == bufA) ? bufB : bufA;
-    // ---- 5. e^{ija} Z_j / Mt on the P grid (Nyquist split evenly), inverse FFT
-    for (int pp = lane; pp < P; pp += 32) Xb[pp] = C(0.0);
-    __syncwarp();
-    for (int jj = lane; jj <= 2 * M; jj += 32) {
-      const int jv = jj - M;
-      cplx z = Z[(jv + Mt) % Mt] * (1.0 / Mt);
-      if (jv == M || jv == -M) z = 0.5 * z;
-      Xb[(jv + P) % P] = ph[jj] * z;
-    }
-    __syncwarp();
-    cplx* Zt = warp_fft(Xb, Z, P, a.tw, a.T, +1);
-    // U_p = F~(phi_p + a) C~(phi_p + a) Acal_p
-    for (int pp = lane; pp < P; pp += 32) Zt[pp] = C(Zt[pp].re * Zt[pp].im * Acal[pp], 0.0);
-    __syncwarp();
-    const cplx* Yf = warp_fft(Zt, (Zt == bufA) ? bufB : bufA, P, a.tw, a.T, -1);
-    for (int mm = lane; mm <= 2 * M; mm += 32) {
-      const int m = mm - M;
-      kc[mm] = conj(ph[mm]) * Yf[(m + P) % P] * (1.0 / P);
-    }
-    __syncwarp();
-    // ---- 6. outputs
-    if (a.modes_out) {
-      for (int q = lane; q < Mt; q += 32) bufA[q] = C(sn[q], 0.0);
-      __syncwarp();
-      const cplx* Sf = warp_fft(bufA, bufB, Mt, a.tw, a.T, -1);
-      double* out = a.modes_out + p * 2 * (Mt + 1);
-      for (int mm = lane; mm <= 2 * M; mm += 32) {
-        const int m = mm - M;
-        cplx sv = Sf[(m + Mt) % Mt] * (1.0 / Mt);
-        if (m == M || m == -M) sv = 0.5 * sv;
-        out[2 * mm] = kc[mm].re - sv.im;
-        out[2 * mm + 1] = kc[mm].im + sv.re;
-      }
-      __syncwarp();
-    }
-    if (a.weights_out) {
-      // Q[m mod Mt] = Kc_m (|m| < M), Q[M] = (Kc_M + Kc_{-M})/2;  W = IFFT(Q)/Mt + i sn/Mt
-      for (int q = lane; q < Mt; q += 32) {
-        const int m = q < M ? q : q - Mt;
-        bufA[q] = (q == M) ? 0.5 * (kc[2 * M] + kc[0]) : kc[m + M];
-      }
-      __syncwarp();
-      const cplx* Wt = warp_fft(bufA, bufB, Mt, a.tw, a.T, +1);
-      for (int q = lane; q < Mt; q += 32) {
-        const cplx w = Wt[q] * (1.0 / Mt);
-        a.weights_out[p * Mt + q] = C(w.re, w.im + sn[q] / Mt);
+      // ---- D11. outputs
+      for (int kidx = 0; kidx < nk; ++kidx) {
+        const bool isS = wantS && kidx == 0;
+        const cplx* sing = isS ? sm.kc : sm.kk;
+        if (a.modes_out) {
+          for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(isS ? sm.sn[q] : sm.bt0[q], 0.0);
+          __syncwarp();
+          const cplx* Sf = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+          double* out = a.modes_out + (p * nk + kidx) * 2 * (Mt + 1);
+          for (int mm = lane; mm <= 2 * M; mm += 32) {
+            const int m = mm - M;
+            cplx sv = Sf[wrapi(m, Mt)] * (1.0 / Mt);
+            if (m == M || m == -M) sv = 0.5 * sv;
+            const cplx smooth = isS ? C(-sv.im, sv.re) : C(sv.im, -sv.re);   // i <sn> or -i <beta tau0>
+            out[2 * mm] = sing[mm].re + smooth.re;
+            out[2 * mm + 1] = sing[mm].im + smooth.im;
+          }
+          __syncwarp();
+        }
+        if (a.weights_out) {
+          for (int q = lane; q < Mt; q += 32) {
+            const int m = q < M ? q : q - Mt;
+            sm.W0[q] = (q == M) ? 0.5 * (sing[2 * M] + sing[0]) : sing[m + M];
+          }
+          __syncwarp();
+          const cplx* Wt = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, +1);
+          cplx* wout = a.weights_out + kidx * a.weights_stride + p * Mt;
+          for (int q = lane; q < Mt; q += 32) {
+            const cplx w = Wt[q] * (1.0 / Mt);
+            const double sv = (isS ? sm.sn[q] : -sm.bt0[q]) / Mt;
+            wout[q] = C(w.re, w.im + sv);
+          }
+          __syncwarp();
+        }
       }
     }
     __syncwarp();
   }
 }
 
-size_t pair_s_smem_per_warp(int Mt) {
-  const int P = 3 * Mt, L = 3 * (Mt / 2);
-  return sizeof(double) * (size_t)(6 * Mt + 5 * P + L + 5);
+// ------------------------------------------------------------------ host side
+static std::vector<double> recurrence_table(int n) {
+  std::vector<double> r(4 * (size_t)n, 0.0);
+  for (int m = 1; m < n; ++m) {
+    const long double mm = m;
+    r[4 * m + 0] = (double)((2 * mm - 1) / (2 * mm + 1));
+    r[4 * m + 1] = (double)((8 * mm) / (2 * mm + 1));
+    r[4 * m + 2] = (double)((4 * mm) / (2 * mm - 1));
+    r[4 * m + 3] = (double)((2 * mm + 1) / (2 * mm - 1));
+  }
+  return r;
 }
 
-PairArgs make_pair_args(bie_surface s, double k) {
-  PairArgs a;
+struct PairResources {
+  double* rec = nullptr;
+  int rec_len = 0;
+  double* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+static PairResources g_res;   // grown on demand (the library drives one device per process)
+
+PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
+  PairArgs a = {};
   a.S = s->sp;
   a.gl = s->gl01;
   a.Np = s->Np;
   a.Mt = s->Mt;
   a.M = s->Mt / 2;
-  a.P = 3 * s->Mt;
+  a.kernels = (int)kernels;
+  const bool withK = kernels & BIE_KERNEL_K;
+  a.P = (withK ? 4 : 3) * s->Mt;
+  a.L = (withK ? 4 : 3) * a.M;
   a.T = s->tw_len;
-  a.L = 3 * a.M;
   a.h = s->h;
   a.k = k;
   a.N = s->N;
@@ -408,38 +813,64 @@ PairArgs make_pair_args(bie_surface s, double k) {
   a.ring_r = s->ring_r;
   a.ring_n = s->ring_n;
   a.tw = s->tw;
-  a.rows = nullptr;
-  a.srcs = nullptr;
-  a.modes_out = nullptr;
-  a.weights_out = nullptr;
   a.status = s->ctx->d_status;
-  a.enumerate = 0;
-  a.p0 = 0;
-  a.n_pairs = 0;
   return a;
 }
 
-bie_status launch_pairs(bie_surface s, const PairArgs& a) {
-  const int warps_per_block = 4;
-  const size_t smem = pair_s_smem_per_warp(s->Mt) * warps_per_block;
-  static int configured_smem = 0;
-  cudaError_t e;
-  if ((int)smem > configured_smem) {
-    e = cudaFuncSetAttribute(pair_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_s_kernel)");
-    configured_smem = (int)smem;
-  }
+int pair_warps_per_block(int Mt, unsigned kernels) {
+  const bool withK = kernels & BIE_KERNEL_K;
+  const int P = (withK ? 4 : 3) * Mt, L = (withK ? 4 : 3) * (Mt / 2);
+  const size_t per = smem_doubles(Mt, P, L, withK) * sizeof(double);
+  int w = (int)(kSmemLimit / per);
+  return w > kMaxWarpsPerBlock ? kMaxWarpsPerBlock : w;
+}
+
+bie_status launch_pairs(bie_surface s, PairArgs& a) {
+  const bool withK = a.kernels & BIE_KERNEL_K;
+  const int wpb = pair_warps_per_block(a.Mt, (unsigned)a.kernels);
+  if (wpb < 1) { set_error("pair kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
+  const size_t smem = smem_doubles(a.Mt, a.P, a.L, withK) * sizeof(double) * wpb;
+  cudaError_t e = cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_kernel)");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_s_kernel, 32 * warps_per_block, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy(pair_s_kernel)");
-  if (per_sm < 1) { set_error("pair kernel does not fit (smem %zu)", smem); return BIE_EUNSUPPORTED; }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel, 32 * wpb, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy(pair_kernel)");
+  if (per_sm < 1) { set_error("pair kernel does not fit (shared memory %zu bytes)", smem); return BIE_EUNSUPPORTED; }
   int64_t blocks = (int64_t)s->ctx->sms * per_sm;
-  const int64_t need = (a.n_pairs + warps_per_block - 1) / warps_per_block;
+  const int64_t need = (a.n_pairs + 32 * wpb - 1) / (32 * wpb);
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  pair_s_kernel<<<(unsigned)blocks, 32 * warps_per_block, smem, s->ctx->stream>>>(a);
+  // recurrence table: Miller needs N < 3.8 L + 17 (it runs only when L b > 7)
+  const int need_rec = (int)(3.8 * a.L) + 64;
+  if (g_res.rec_len < need_rec) {
+    std::vector<double> r = recurrence_table(need_rec);
+    cudaStreamSynchronize(s->ctx->stream);
+    if (g_res.rec) cudaFree(g_res.rec);
+    g_res.rec = nullptr;
+    g_res.rec_len = 0;
+    e = cudaMalloc((void**)&g_res.rec, sizeof(double) * r.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(recurrence table)");
+    e = cudaMemcpy(g_res.rec, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(recurrence table)");
+    g_res.rec_len = need_rec;
+  }
+  a.scratch_per_warp = (int64_t)2 * (a.L + 1) * 32;
+  const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
+  if (g_res.scratch_bytes < sbytes) {
+    cudaStreamSynchronize(s->ctx->stream);
+    if (g_res.scratch) cudaFree(g_res.scratch);
+    g_res.scratch = nullptr;
+    g_res.scratch_bytes = 0;
+    e = cudaMalloc((void**)&g_res.scratch, sbytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pair scratch)");
+    g_res.scratch_bytes = sbytes;
+  }
+  a.rec = g_res.rec;
+  a.rec_len = g_res.rec_len;
+  a.scratch = g_res.scratch;
+  pair_kernel<<<(unsigned)blocks, 32 * wpb, smem, s->ctx->stream>>>(a);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "pair_s_kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch");
   return BIE_OK;
 }
 
@@ -450,17 +881,17 @@ using namespace bie;
 extern "C" bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
                                        const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
                                        double* modes_out) {
-  if (!ctx || !s || (n_pairs > 0 && (!pair_row || !pair_src || !modes_out)) || n_pairs < 0) {
+  if (!ctx || !s || n_pairs < 0 || (n_pairs > 0 && (!pair_row || !pair_src || !modes_out))) {
     set_error("bie_kernel_modes: invalid arguments");
     return BIE_EINVAL;
   }
   if (!(k > 0) || !(k < 1e6)) { set_error("bie_kernel_modes: k must be in (0, 1e6)"); return BIE_EINVAL; }
-  if (kernels != BIE_KERNEL_S) {
-    set_error("bie_kernel_modes: this build computes BIE_KERNEL_S");
-    return BIE_EUNSUPPORTED;
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
+    set_error("bie_kernel_modes: bad kernel mask %u", kernels);
+    return BIE_EINVAL;
   }
   if (n_pairs == 0) return BIE_OK;
-  PairArgs a = make_pair_args(s, k);
+  PairArgs a = make_pair_args(s, k, kernels);
   a.rows = pair_row;
   a.srcs = pair_src;
   a.n_pairs = n_pairs;

@@ -23,19 +23,24 @@ def ctx(bie):
     return bie.Context()
 
 
-def _check(bie, ctx, ggq, surface, Np, Mt, k, n, seed=0):
+def _check(bie, ctx, ggq, surface, Np, Mt, k, n, seed=0, kernels=("S",)):
     s = bie.Surface(ctx, surface, Np, Mt, ggq)
     rows, srcs = sample_pairs(Np, Mt, n, seed)
-    out = bie.kernel_modes(s, bie.KERNEL_S, k, torch.from_numpy(rows).cuda(), torch.from_numpy(srcs).cuda())
+    mask = (bie.KERNEL_S if "S" in kernels else 0) | (bie.KERNEL_K if "K" in kernels else 0)
+    out = bie.kernel_modes(s, mask, k, torch.from_numpy(rows).cuda(), torch.from_numpy(srcs).cuda())
     ctx.sync()
-    gpu = out[:, 0, :].cpu().numpy()
     t, th, ts = pair_geometry(Np, Mt, rows, srcs, ggq[0])
-    ref = np.concatenate([km.method_modes(surface, t[c:c + 256], th[c:c + 256], ts[c:c + 256], Mt, k)["S"]
-                          for c in range(0, len(t), 256)])
-    err = np.max(np.abs(gpu - ref), axis=1) / np.max(np.abs(ref), axis=1)
-    assert np.all(np.isfinite(gpu))
-    assert err.max() <= TOL, "worst pair %d: %.3e" % (err.argmax(), err.max())
-    return err
+    chunks = [km.method_modes(surface, t[c:c + 256], th[c:c + 256], ts[c:c + 256], Mt, k, tuple(kernels))
+              for c in range(0, len(t), 256)]
+    worst = 0.0
+    for idx, kd in enumerate(kernels):
+        gpu = out[:, idx, :].cpu().numpy()
+        ref = np.concatenate([ch[kd] for ch in chunks])
+        err = np.max(np.abs(gpu - ref), axis=1) / np.max(np.abs(ref), axis=1)
+        assert np.all(np.isfinite(gpu))
+        assert err.max() <= TOL, "%s: worst pair %d: %.3e" % (kd, err.argmax(), err.max())
+        worst = max(worst, err.max())
+    return worst
 
 
 def test_sphere_general_path(bie, ctx, ggq):
@@ -54,6 +59,16 @@ def test_ragged_small_grids(bie, ctx, ggq):
     # Mth with a factor 3 (radix-3 passes) and the smallest grid
     _check(bie, ctx, ggq, wl.ellipsoid(1.0, 0.8, 0.6), 3, 24, 2.0, 300)
     _check(bie, ctx, ggq, wl.sphere(), 2, 8, 1.0, 200)
+
+
+@pytest.mark.parametrize("surface,Np,Mt,k", [(wl.sphere(), 4, 32, 1.0), (wl.ellipsoid(1.0, 0.8, 0.6), 16, 128, 10.0),
+                                             (wl.bumpy(), 6, 96, 5.0)])
+def test_double_layer_and_single_layer_together(bie, ctx, ggq, surface, Np, Mt, k):
+    _check(bie, ctx, ggq, surface, Np, Mt, k, 300, seed=2, kernels=("S", "K"))
+
+
+def test_double_layer_alone(bie, ctx, ggq):
+    _check(bie, ctx, ggq, wl.ellipsoid(1.0, 0.8, 0.6), 3, 24, 2.0, 300, seed=3, kernels=("K",))
 
 
 def test_invalid_pair_reports_error(bie, ctx, ggq):

@@ -22,15 +22,16 @@ def ctx(bie):
     return bie.Context()
 
 
+@pytest.mark.parametrize("op", ["S", "CFIE"])
 @pytest.mark.parametrize("surface,Np,Mt,k", [(wl.sphere(), 4, 32, 1.0), (wl.ellipsoid(1.0, 0.8, 0.6), 5, 48, 4.0),
                                              (wl.bumpy(), 4, 64, 3.0)])
-def test_assembled_rows_match_oracle(bie, ctx, ggq, surface, Np, Mt, k):
+def test_assembled_rows_match_oracle(bie, ctx, ggq, surface, Np, Mt, k, op):
     s = bie.Surface(ctx, surface, Np, Mt, ggq)
-    A = bie.assemble(s, bie.OP_S, k)
+    A = bie.assemble(s, bie.OP_S if op == "S" else bie.OP_CFIE, k)
     ctx.sync()
     rows = wl.sample_rows(Np, Mt, 40)
     rows = np.unique(np.concatenate([rows, [0, s.N - 1, 16 * Mt - 1, 16 * Mt]]))
-    ref = ny.operator_rows(surface, Np, Mt, k, ggq[0], ggq[1], rows, op="S")
+    ref = ny.operator_rows(surface, Np, Mt, k, ggq[0], ggq[1], rows, op=op, eta=k)
     got = A[torch.from_numpy(rows).cuda()].cpu().numpy()
     err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
     assert err.max() <= 1e-12, err.max()
@@ -71,6 +72,20 @@ def test_mixed_precision_solve_reaches_tolerance(bie, ctx, ggq):
     for x in (x64, x32):
         u = bie.field_eval(s, bie.OP_S, k, x, pts).cpu().numpy()
         assert np.linalg.norm(u - ue) / np.linalg.norm(ue) <= 1e-6
+
+
+def test_cfie_exterior_point_source(bie, ctx, ggq):
+    # exterior Dirichlet problem through the combined-field operator I + K - i k S
+    k, src = 4.0, [0.1, 0.1, -0.05]
+    surf = wl.ellipsoid(1.0, 0.8, 0.6)
+    s = bie.Surface(ctx, surf, 6, 48, ggq)
+    A = bie.assemble(s, bie.OP_CFIE, k)
+    x, rep = bie.solve(ctx, A, bie.rhs(s, 1, src, k), tol=1e-11)
+    pts = wl.exterior_points(10, 3.0)
+    u = bie.field_eval(s, bie.OP_CFIE, k, x, pts).cpu().numpy()
+    ue = exact.point_source(k, pts, src)
+    assert np.linalg.norm(u - ue) / np.linalg.norm(ue) <= 1e-7
+    assert rep["iterations"] < 400
 
 
 def test_solver_reports_nonconvergence(bie, ctx, ggq):

@@ -86,3 +86,12 @@ def test_b_modes_satisfy_paper_forward_recurrence_where_it_is_stable():
     for m in range(1, 20):
         rec = np.cosh(b) * B[0, m - 1] - (2 * m - 1) / 2 * np.exp(b) * A[0, m - 1]
         assert abs(B[0, m] - rec) <= 1e-12 * B[0, 0]
+
+
+@pytest.mark.parametrize("b", [4e-5, 0.01, 0.3])
+def test_b_difference_identity(b):
+    # B_{m-1} - B_{m+1} = <2i sin(th) s^{-3/2}>_m = 2 m e^b A_m  (from d/dth s^{-1/2} = -e^{-b} sin th s^{-3/2});
+    # checked against independent quadrature of both B's
+    A, _ = sp.a_modes(np.array([b]), 12)
+    for m in (1, 4):
+        assert abs(2 * m * np.exp(b) * A[0, m] - (_b_quad(m - 1, b) - _b_quad(m + 1, b))) <= 1e-9 * abs(_b_quad(m, b)) * b
