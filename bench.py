@@ -291,7 +291,8 @@ def run_kernel_only(n):
     surf = bie.Surface(ctx, c["surface"], c["Np"], c["Mt"], wl.load_ggq())
     rows = (16 * c["Mt"] * (c["Np"] // 2) + torch.arange(n, device="cuda", dtype=torch.int64) // 48)
     srcs = (torch.arange(n, device="cuda", dtype=torch.int32) % 48)
-    out = bie.kernel_modes(surf, bie.KERNEL_S, c["k"], rows, srcs)
+    kern = bie.KERNEL_S | (bie.KERNEL_K if os.environ.get("BENCH_KERNELS", "S") == "SK" else 0)
+    out = bie.kernel_modes(surf, kern, c["k"], rows, srcs)
     ctx.sync()
     print("kernel-only: %d pairs, finite: %s" % (n, bool(torch.isfinite(torch.view_as_real(out)).all())))
 

@@ -112,25 +112,37 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
   }
   const int Mt = s->Mt;
   const int nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + ((kernels & BIE_KERNEL_K) ? 1 : 0);
-  const int64_t chunk_pairs = (int64_t)16 * 48 * Mt;
+  const int64_t panel_pairs = (int64_t)16 * 48 * Mt;
+  // panels per launch: enough pairs for many waves, weight buffer at most ~4 GB
+  const size_t per_panel_bytes = sizeof(cplx) * (size_t)panel_pairs * Mt * nk;
+  int group = (int)(((size_t)4 << 30) / per_panel_bytes);
+  if (group < 1) group = 1;
+  if (group > s->Np) group = s->Np;
+  const int64_t chunk_pairs = panel_pairs * group;
   cplx* W = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt * nk, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(weights)");
   bie_status st = BIE_OK;
   const cplx sS = C(ws_re, ws_im) * (0.5 * s->h), sK = C(wk_re, wk_im) * (0.5 * s->h);
-  const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
-  const cplx* WK = (kernels & BIE_KERNEL_K) ? W + (nk - 1) * chunk_pairs * Mt : nullptr;
-  for (int j = 0; j < s->Np && st == BIE_OK; ++j) {
+  for (int j0 = 0; j0 < s->Np && st == BIE_OK; j0 += group) {
+    const int nj = (j0 + group <= s->Np) ? group : s->Np - j0;
     PairArgs a = make_pair_args(s, k, kernels);
     a.enumerate = 1;
-    a.p0 = (int64_t)j * chunk_pairs;
-    a.n_pairs = chunk_pairs;
+    a.p0 = (int64_t)j0 * panel_pairs;
+    a.n_pairs = panel_pairs * nj;
     a.weights_out = W;
-    a.weights_stride = chunk_pairs * Mt;
+    a.weights_stride = panel_pairs * nj * Mt;
     st = launch_pairs(s, a);
     if (st != BIE_OK) break;
-    dim3 grid(16 * Mt, 3);
-    near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j, sS, sK, s->near_coef, WS, WK, (cplx*)A_out);
+    const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
+    const cplx* WK = (kernels & BIE_KERNEL_K) ? W + (nk - 1) * a.weights_stride : nullptr;
+    for (int jj = 0; jj < nj; ++jj) {
+      const int64_t off = (int64_t)jj * panel_pairs * Mt;
+      dim3 grid(16 * Mt, 3);
+      near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
+                                                       WS ? WS + off : nullptr, WK ? WK + off : nullptr,
+                                                       (cplx*)A_out);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");
   }

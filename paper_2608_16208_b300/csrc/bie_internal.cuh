@@ -111,7 +111,7 @@ __device__ __forceinline__ void scpow_d(double st, double ct, int p, int q, doub
 struct Geo {
   R3 r, rt, rth, rtt, rtth, rthth;
 };
-__device__ inline void surf_eval(const SurfP& S, double t, double th, int order, Geo* g) {
+static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double th, int order, Geo* g) {
   double st, ct, sp, cp;
   sincos(t, &st, &ct);
   sincos(th, &sp, &cp);
@@ -169,7 +169,7 @@ __device__ inline void surf_eval(const SurfP& S, double t, double th, int order,
 }
 
 // r, r_t, r_th at real t and complex th (analytic continuation in theta).
-__device__ inline void surf_eval_c(const SurfP& S, double t, cplx th, C3* r, C3* rt, C3* rth) {
+static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx th, C3* r, C3* rt, C3* rth) {
   double st, ct;
   sincos(t, &st, &ct);
   cplx cp, sp;
@@ -210,7 +210,8 @@ struct GL16 {
   double x[16], w[16];
 };
 
-__device__ __forceinline__ double wrap_pi(double d) { return d - kTwoPi * rint(d / kTwoPi); }
+constexpr double kInvTwoPi = 0.15915494309189533576888376337251436;
+__device__ __forceinline__ double wrap_pi(double d) { return d - kTwoPi * rint(d * kInvTwoPi); }
 
 // r(t_s, th_s) - r(t, th) for complex th_s by the line integral of the first
 // derivatives along gamma(lam) = v + lam (u - v) (Section 4, Remark).
@@ -253,7 +254,7 @@ __host__ __device__ inline FFTPlan make_plan(int n) {
 // In-place (returns pointer to the buffer holding the result) transform of x[0..n)
 // using y as scratch.  sign = -1: X_k = sum x_j e^{-2 pi i jk/n}; sign = +1: inverse
 // (unnormalised).  Called by all 32 lanes of a warp.
-__device__ inline cplx* warp_fft(cplx* x, cplx* y, int n, const cplx* __restrict__ tw, int T, int sign) {
+static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cplx* __restrict__ tw, int T, int sign) {
   const int lane = threadIdx.x & 31;
   const FFTPlan p = make_plan(n);
   cplx* src = x;
@@ -333,6 +334,7 @@ struct bie_surface_s {
   double* near_coef;   // [dev] [3][16][16][16] = w_g L_n(x_g) on the reference panel
   double* ggq_x;       // [dev] [3][16][16]
   bie::cplx* tw;       // [dev] twiddles for length 12 Mt
+  double* thgrid;      // [dev] [Mt][3]: th_q = 2 pi q / Mt, sin(th_q/2), cos(th_q/2)
   int tw_len;
   double* host_t_nodes;
   double gl_x[16], gl_w[16];   // Gauss-Legendre rule on [-1, 1] from the caller's tables

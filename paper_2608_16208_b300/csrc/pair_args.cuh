@@ -18,6 +18,7 @@ struct PairArgs {
   const double* ring_r;
   const double* ring_n;
   const cplx* tw;
+  const double* thg;              // [Mt][3]: th_q, sin(th_q/2), cos(th_q/2)
   const double* rec;              // recurrence coefficient table, 4 doubles per m (see pair_modes.cu)
   int rec_len;
   double* scratch;                // per resident warp: (L + 1) x 32 doubles (A), + (L + 1) x 32 (D) if K

@@ -65,7 +65,7 @@ __device__ __forceinline__ double ipow(double x, int n) {
 
 // r(t_s, ths) - r(t, th) without cancellation (sum-to-product identities); ths real or complex.
 template <typename T>
-__device__ V3<T> diff_ana(const SurfP& S, double ts, T ths, double t, double th) {
+__device__ __noinline__ V3<T> diff_ana(const SurfP& S, double ts, T ths, double t, double th) {
   double s1, c1, s0, c0, smt, cmt;
   sincos(ts, &s1, &c1);
   sincos(t, &s0, &c0);
@@ -151,9 +151,9 @@ __device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, cplx z, cplx
   *df = 2.0 * (Y.x * rth.x + Y.y * rth.y + Y.z * rth.z);
 }
 
-__device__ inline void locate_root(const SurfP& S, int Mt, PairInfo& P) {
+__device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
   const double hgrid = kTwoPi / Mt;
-  double a0 = kTwoPi * P.bi / Mt;
+  double a0 = kTwoPi * P.bi / Mt;   // same value as the theta table entry
   const double start = a0;
   double g0 = 0, g1 = 0, g2 = 0;
   auto eval_r = [&](double z) {
@@ -208,8 +208,9 @@ __device__ inline void locate_root(const SurfP& S, int Mt, PairInfo& P) {
 
 // ------------------------------------------------------------------ phase C: A_m, D_m (one lane)
 // rec[4m..4m+3] = (2m-1)/(2m+1), 8m/(2m+1), 4m/(2m-1), (2m+1)/(2m-1)
-__device__ inline void a_modes_lane(double b, int L, const double* __restrict__ rec, int rec_len, double* A,
+__device__ __noinline__ void a_modes_lane(double b, int L, const double* __restrict__ rec, int rec_len, double* A,
                                     double* D, int stride) {
+  // D may be null (only A is needed for the single-layer kernel)
   const double q = exp(-b);
   double K, E;
   ellipke(q * q, -expm1(-2 * b), &K, &E);
@@ -218,15 +219,15 @@ __device__ inline void a_modes_lane(double b, int L, const double* __restrict__ 
   if (L * b <= kForwardLimit) {
     double am = A0, dm = (2 / kPi) * ((K - E) / q - K);
     A[0] = am;
-    D[0] = -dm;
+    if (D) D[0] = -dm;
     am += dm;
     A[stride] = am;
-    D[stride] = dm;
+    if (D) D[stride] = dm;
     for (int m = 1; m < L; ++m) {
       dm = rec[4 * m] * dm + (rec[4 * m + 1] * sh2) * am;
       am += dm;
       A[(m + 1) * stride] = am;
-      D[(m + 1) * stride] = dm;
+      if (D) D[(m + 1) * stride] = dm;
     }
     return;
   }
@@ -251,10 +252,10 @@ __device__ inline void a_modes_lane(double b, int L, const double* __restrict__ 
   for (int m = 0; m <= L; ++m) {
     const double am = A[m * stride] * f;
     A[m * stride] = am;
-    if (m) D[m * stride] = am - prevA;
+    if (D && m) D[m * stride] = am - prevA;
     prevA = am;
   }
-  D[0] = A[0] - A[stride];
+  if (D) D[0] = A[0] - A[stride];
 }
 
 // ------------------------------------------------------------------ small helpers of phase D
@@ -324,7 +325,7 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
 
 // e^{ija} Z_j / Mt (j = -M..M, Nyquist split evenly) placed on the P grid in X, inverse
 // transform with scratch Y; returns the buffer holding the result.
-__device__ inline cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y, int Mt, int P, const cplx* tw,
+__device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y, int Mt, int P, const cplx* tw,
                                  int T) {
   const int lane = threadIdx.x & 31;
   const int M = Mt / 2;
@@ -341,12 +342,14 @@ __device__ inline cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y
 }
 
 // ------------------------------------------------------------------ the kernel
+template <bool kWithK>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const PairArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
-  const bool wantS = a.kernels & BIE_KERNEL_S, wantK = a.kernels & BIE_KERNEL_K;
+  const bool wantS = a.kernels & BIE_KERNEL_S;
+  constexpr bool wantK = kWithK;
   const size_t per_warp = smem_doubles(Mt, P, L, wantK);
   Smem sm = carve(smem + per_warp * wib, Mt, P, L, wantK);
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       if (pr.valid) {
         pr.ring = (tn * 3 + d) * 16 + g;
         pr.t = a.t_nodes[tn];
-        pr.th = kTwoPi * (int)(row % Mt) / Mt;
+        pr.th = a.thg[3 * (int)(row % Mt)];
         pr.ts = a.ring_t[pr.ring];
         pr.x = a.pts[3 * row];
         pr.y = a.pts[3 * row + 1];
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       const double dts = fabs(pr.t - pr.ts);
       double bv = INFINITY;
       for (int q = lane; q < Mt; q += 32) {
-        const double thq = kTwoPi * q / Mt;
+        const double thq = a.thg[3 * q];
         double r2;
         if (dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta) {
           const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
@@ -437,10 +440,11 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       sm.info[lane].b = pr.b;
       sm.info[lane].a0 = pr.a0;
       sm.info[lane].capped = pr.capped;
-      a_modes_lane(pr.b, L, a.rec, a.rec_len, scrA + lane, scrD + lane, 32);
+      a_modes_lane(pr.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32);
     }
     __syncwarp();
     // ---------------- D. per pair (warp)
+    int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = sm.info[pi];
       const int64_t p = p0 + pi;
@@ -463,6 +467,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
         sm.Atab[m] = scrA[m * 32 + pi];
         if (wantK) sm.Dtab[m] = scrD[m * 32 + pi];
       }
+      // e^{ija}, j = -M..M, each from its own sincos: the translated tau_3 combines phase-weighted
+      // terms that cancel, so a rotation recurrence's ulp drift would be amplified
       for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
       __syncwarp();
       if (wantK) {  // B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b, m = 0..2M+1
@@ -472,7 +478,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
           sm.Btab[m] = -(m - 0.5) * fac * (sm.Dtab[m] + 2 * sh2b * sm.Atab[m]);
         __syncwarp();
       }
-      // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and, with K, B_{|d|} or B~_{|d|} (|d| <= 2M)
+      // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and, with K, B_{|d|} or B~_{|d|} (|d| <= 2M).
+      // Single layer alone: the transform of this pair's circulant usually arrived packed with the
+      // previous pair's Toeplitz transform (acal_next); compute it here only when it did not.
+      if (!wantK && acal_next == pi) {
+        // already in Acal
+      } else {
       for (int pp = lane; pp < P; pp += 32) {
         const int dd = pp <= P / 2 ? pp : P - pp;
         const double av = dd <= L ? sm.Atab[dd] : 0.0;
@@ -492,9 +503,12 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
         }
       }
       __syncwarp();
+      }
       // ---- D3. samples
+      double sha, cha;   // sin(a/2), cos(a/2)
+      sincos(0.5 * ra, &sha, &cha);
       for (int q = lane; q < Mt; q += 32) {
-        const double thq = kTwoPi * q / Mt;
+        const double thq = a.thg[3 * q];
         const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta;
         double yx, yy, yz;
         if (near) {
@@ -504,15 +518,19 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
           yx = rr[3 * q] - pr.x; yy = rr[3 * q + 1] - pr.y; yz = rr[3 * q + 2] - pr.z;
         }
         const double r2 = yx * yx + yy * yy + yz * yz;
-        const double rho = sqrt(r2);
-        const double sp = sin(0.5 * (thq - ra));
+        const double rinv = rsqrt(r2);
+        const double rho = r2 * rinv;
+        // sin((th_q - a)/2): direct where th_q - a is small (exact difference, relative accuracy),
+        // angle addition from the table elsewhere
+        const double dq = thq - ra;
+        const double sp = fabs(dq) < 0.1 ? sin(0.5 * dq) : a.thg[3 * q + 1] * cha - a.thg[3 * q + 2] * sha;
         const double s = om * om + 4 * qb * sp * sp;
-        const double F = sqrt(s / r2);
+        const double F = sqrt(s) * rinv;
         double skr, ckr;
         sincos(a.k * rho, &skr, &ckr);
         sm.rho2[q] = r2;
         sm.W0[q] = C(F, ckr);          // F + i cos(k rho)
-        sm.sn[q] = skr / rho;
+        sm.sn[q] = skr * rinv;
         if (wantK) {
           const double x = a.k * rho;
           double al, be;
@@ -547,7 +565,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
         for (int c0 = -Kw; c0 <= Kw; c0 += 2) {
           const int c = c0 + (lane >> 4);
           const int q = wrapi(i + c, Mt);
-          const double thq = kTwoPi * q / Mt;
+          const double thq = a.thg[3 * q];
           const double dth = wrap_pi(pr.th - thq);
           const bool nearq = (c <= Kw) && (dts + fabs(dth) <= kStableDelta);
           if (!__ballot_sync(0xffffffffu, nearq)) continue;
@@ -594,7 +612,34 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       cplx* uf = (up1 == sm.W0) ? sm.W1 : sm.W0;
       if (wantK)
         for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up1[pp].re;   // keep F~ for V_K
-      if (wantS) {
+      if (wantS && !wantK) {
+        // U = F~ C~ Acal (real) in the real part; the next valid pair's circulant A_{|d|} (real, even)
+        // in the imaginary part: one transform serves both
+        int nxt = pi + 1;
+        while (nxt < nb && !sm.info[nxt].valid) ++nxt;
+        const bool pack = nxt < nb;
+        for (int pp = lane; pp < P; pp += 32) {
+          const int dd = pp <= P / 2 ? pp : P - pp;
+          const double an = (pack && dd <= L) ? scrA[dd * 32 + nxt] : 0.0;
+          uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], an);
+        }
+        __syncwarp();
+        const cplx* Yf = warp_fft(uf, up1, P, a.tw, a.T, -1);
+        for (int jj = lane; jj <= 2 * M; jj += 32) {
+          const int m = jj - M;
+          const cplx zp = Yf[wrapi(m, P)], zm = conj(Yf[wrapi(-m, P)]);
+          sm.kc[jj] = conj(sm.ph[jj]) * (0.5 * (zp + zm)) * (1.0 / P);
+        }
+        if (pack) {
+          __syncwarp();
+          // transform of the (real, even) circulant = (Z_p - conj Z_{-p}) / (2i), real
+          for (int pp = lane; pp < P; pp += 32) {
+            const cplx zp = Yf[pp], zm = conj(Yf[(P - pp) % P]);
+            sm.Acal[pp] = 0.5 * (zp.im - zm.im);
+          }
+          acal_next = nxt;
+        }
+      } else if (wantS) {
         for (int pp = lane; pp < P; pp += 32) uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], 0.0);
         __syncwarp();
         const cplx* Yf = warp_fft(uf, up1, P, a.tw, a.T, -1);
@@ -813,6 +858,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.ring_r = s->ring_r;
   a.ring_n = s->ring_n;
   a.tw = s->tw;
+  a.thg = s->thgrid;
   a.status = s->ctx->d_status;
   return a;
 }
@@ -830,10 +876,11 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
   const int wpb = pair_warps_per_block(a.Mt, (unsigned)a.kernels);
   if (wpb < 1) { set_error("pair kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
   const size_t smem = smem_doubles(a.Mt, a.P, a.L, withK) * sizeof(double) * wpb;
-  cudaError_t e = cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = withK ? pair_kernel<true> : pair_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_kernel)");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel, 32 * wpb, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy(pair_kernel)");
   if (per_sm < 1) { set_error("pair kernel does not fit (shared memory %zu bytes)", smem); return BIE_EUNSUPPORTED; }
   int64_t blocks = (int64_t)s->ctx->sms * per_sm;
@@ -854,7 +901,7 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(recurrence table)");
     g_res.rec_len = need_rec;
   }
-  a.scratch_per_warp = (int64_t)2 * (a.L + 1) * 32;
+  a.scratch_per_warp = (int64_t)(withK ? 2 : 1) * (a.L + 1) * 32;
   const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
   if (g_res.scratch_bytes < sbytes) {
     cudaStreamSynchronize(s->ctx->stream);
@@ -868,7 +915,7 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
   a.rec = g_res.rec;
   a.rec_len = g_res.rec_len;
   a.scratch = g_res.scratch;
-  pair_kernel<<<(unsigned)blocks, 32 * wpb, smem, s->ctx->stream>>>(a);
+  kern<<<(unsigned)blocks, 32 * wpb, smem, s->ctx->stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch");
   return BIE_OK;

@@ -150,6 +150,13 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
     tw[k] = C((double)cosl(a), (double)sinl(a));
   }
   s->tw_len = T;
+  std::vector<double> thg(3 * Mt);
+  for (int q = 0; q < Mt; ++q) {
+    const double th = kTwoPi * q / Mt;
+    thg[3 * q] = th;
+    thg[3 * q + 1] = sin(0.5 * th);
+    thg[3 * q + 2] = cos(0.5 * th);
+  }
   s->host_t_nodes = new double[16 * Np];
   memcpy(s->host_t_nodes, tn.data(), sizeof(double) * 16 * Np);
   cudaError_t e;
@@ -167,6 +174,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   ALLOC(s->near_coef, sizeof(double) * coef.size());
   ALLOC(s->ggq_x, sizeof(double) * 3 * 16 * 16);
   ALLOC(s->tw, sizeof(cplx) * T);
+  ALLOC(s->thgrid, sizeof(double) * 3 * Mt);
 #undef ALLOC
   cudaStream_t st = ctx->stream;
 #define H2D(dst, src, bytes)                                                          \
@@ -177,6 +185,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   H2D(s->near_coef, coef.data(), sizeof(double) * coef.size());
   H2D(s->ggq_x, &ggq->x[0][0][0], sizeof(double) * 3 * 16 * 16);
   H2D(s->tw, tw.data(), sizeof(cplx) * T);
+  H2D(s->thgrid, thg.data(), sizeof(double) * 3 * Mt);
 #undef H2D
   const int threads = 256;
   const int blocks = ctx->sms * 8;
@@ -195,7 +204,7 @@ void bie_surface_free(bie_surface s) {
   if (!s) return;
   cudaFree(s->t_nodes); cudaFree(s->pts); cudaFree(s->nrm); cudaFree(s->jac);
   cudaFree(s->ring_t); cudaFree(s->ring_r); cudaFree(s->ring_n);
-  cudaFree(s->near_coef); cudaFree(s->ggq_x); cudaFree(s->tw);
+  cudaFree(s->near_coef); cudaFree(s->ggq_x); cudaFree(s->tw); cudaFree(s->thgrid);
   delete[] s->host_t_nodes;
   delete s;
 }
