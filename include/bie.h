@@ -134,6 +134,32 @@ bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double
                             const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
                             double* modes_out);
 
+/* bie_kernel_modes_noalloc: the same computation as bie_kernel_modes, for
+ * callers that must not allocate device memory -- for example code running
+ * while another allocator holds the whole device (a framework's caching
+ * allocator), or a latency-critical path where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  The paper has no counterpart; this is a
+ * property of the library.  bie_kernel_modes grows a device work buffer (the
+ * per-warp A_m / D_m tables of the recurrences) with cudaMalloc on demand;
+ * this entry point uses a fixed array in the library's device image instead
+ * (16.8 MB, held on every device that loads the library until the process
+ * exits) and calls no cudaMalloc, cudaFree or allocating routine.
+ *   Limit: Mth <= 128 (BIE_EINVAL with a message otherwise); any n_pairs (a
+ *   fixed grid of 32 CTAs loops over them, so it is slower than
+ *   bie_kernel_modes on large inputs).
+ *   The first call on a device takes the device addresses of the arrays and
+ *   copies the recurrence coefficients into them (cudaGetSymbolAddress,
+ *   cudaMemcpyToSymbol) with that device current; make that first call before
+ *   any stream capture.
+ *   All calls share the arrays: calls that may overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller.
+ *   Nothing in the arrays needs clearing between calls: every table entry is
+ *   written before it is read within a call.
+ * Arguments, layouts and other errors as bie_kernel_modes.                     */
+bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                                    const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
+                                    double* modes_out);
+
 /* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------
  * Fill the dense N x N matrix of operator op acting on the weighted density:
  * preparation stage (Gauss-Legendre x trapezoid for every block) and

@@ -64,6 +64,7 @@ _sig("bie_surface_points", _vp, [_vp])
 _sig("bie_surface_normals", _vp, [_vp])
 _sig("bie_surface_jacobians", _vp, [_vp])
 _sig("bie_kernel_modes", _i32, [_vp, _vp, _u, _d, _vp, _vp, _i64, _vp])
+_sig("bie_kernel_modes_noalloc", _i32, [_vp, _vp, _u, _d, _vp, _vp, _i64, _vp])
 
 
 class BieError(RuntimeError):

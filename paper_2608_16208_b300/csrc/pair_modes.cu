@@ -945,3 +945,88 @@ extern "C" bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kern
   a.modes_out = modes_out;
   return launch_pairs(s, a);
 }
+
+// ------------------------------------------------------------------ allocation-free variant
+// For callers that must not allocate device memory.  The pair kernel's scratch (the
+// A_m / D_m tables of every resident warp) and the recurrence coefficient table live in
+// file-scope device arrays, sized for Mth <= kNoAllocMaxMt and a fixed grid of
+// kNoAllocBlocks CTAs of kMaxWarpsPerBlock warps (the grid-stride loop covers any number
+// of pairs).  Every call shares these arrays.
+namespace bie {
+constexpr int kNoAllocMaxMt = 128;
+constexpr int kNoAllocBlocks = 32;
+constexpr int kNoAllocMaxL = 2 * kNoAllocMaxMt;                 // L = 4M with the double layer
+constexpr int kNoAllocRecLen = (int)(3.8 * kNoAllocMaxL) + 64;
+constexpr size_t kNoAllocScratchDoubles =
+    (size_t)kNoAllocBlocks * kMaxWarpsPerBlock * 2 * (kNoAllocMaxL + 1) * 32;   // 16.8 MB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static __device__ __align__(256) double g_noalloc_rec[4 * kNoAllocRecLen];
+
+struct NoAllocState {
+  bool ready = false;
+  double* scratch = nullptr;
+  double* rec = nullptr;
+};
+static NoAllocState g_noalloc[64];   // per device ordinal
+}  // namespace bie
+
+extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                                               const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
+                                               double* modes_out) {
+  if (!ctx || !s || n_pairs < 0 || (n_pairs > 0 && (!pair_row || !pair_src || !modes_out))) {
+    set_error("bie_kernel_modes_noalloc: invalid arguments");
+    return BIE_EINVAL;
+  }
+  if (!(k > 0) || !(k < 1e6)) { set_error("bie_kernel_modes_noalloc: k must be in (0, 1e6)"); return BIE_EINVAL; }
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
+    set_error("bie_kernel_modes_noalloc: bad kernel mask %u", kernels);
+    return BIE_EINVAL;
+  }
+  if (s->Mt > kNoAllocMaxMt) {
+    set_error("bie_kernel_modes_noalloc: m_theta %d exceeds the fixed maximum %d of the static scratch", s->Mt,
+              kNoAllocMaxMt);
+    return BIE_EINVAL;
+  }
+  if (ctx->device < 0 || ctx->device >= 64) { set_error("bie_kernel_modes_noalloc: device ordinal out of range"); return BIE_EINVAL; }
+  if (n_pairs == 0) return BIE_OK;
+  NoAllocState& st = g_noalloc[ctx->device];
+  if (!st.ready) {
+    // once per device, with that device current: device addresses of the static arrays and the
+    // recurrence coefficients (a copy into the static table, no allocation)
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != ctx->device) {
+      set_error("bie_kernel_modes_noalloc: the context's device (%d) is not current (%d)", ctx->device, cur);
+      return BIE_EINVAL;
+    }
+    e = cudaGetSymbolAddress((void**)&st.scratch, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    e = cudaGetSymbolAddress((void**)&st.rec, g_noalloc_rec);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(recurrence table)");
+    const std::vector<double> r = recurrence_table(kNoAllocRecLen);
+    e = cudaMemcpyToSymbol(g_noalloc_rec, r.data(), sizeof(double) * r.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyToSymbol(recurrence table)");
+    st.ready = true;
+  }
+  PairArgs a = make_pair_args(s, k, kernels);
+  a.rows = pair_row;
+  a.srcs = pair_src;
+  a.n_pairs = n_pairs;
+  a.modes_out = modes_out;
+  const bool withK = kernels & BIE_KERNEL_K;
+  const int wpb = pair_warps_per_block(a.Mt, kernels);   // <= kMaxWarpsPerBlock, the scratch sizing
+  if (wpb < 1) { set_error("bie_kernel_modes_noalloc: shared memory does not fit"); return BIE_EUNSUPPORTED; }
+  const size_t smem = smem_doubles(a.Mt, a.P, a.L, withK) * sizeof(double) * wpb;
+  auto kern = withK ? pair_kernel<true> : pair_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_kernel)");
+  a.rec = st.rec;
+  a.rec_len = kNoAllocRecLen;
+  a.scratch = st.scratch;
+  a.scratch_per_warp = (int64_t)(withK ? 2 : 1) * (a.L + 1) * 32;   // <= 2 (kNoAllocMaxL + 1) 32
+  kern<<<kNoAllocBlocks, 32 * wpb, smem, ctx->stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch (no-alloc)");
+  return BIE_OK;
+}
