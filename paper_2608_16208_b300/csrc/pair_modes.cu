@@ -140,6 +140,27 @@ struct PairInfo {
   int valid, bi, capped, pad;
 };
 
+// the batch info lives in registers (lane p holds pair p); a pass over the batch broadcasts it
+__device__ __forceinline__ PairInfo bcast(const PairInfo& p, int src) {
+  PairInfo o;
+  o.row = __shfl_sync(0xffffffffu, (long long)p.row, src);
+  o.ring = __shfl_sync(0xffffffffu, (long long)p.ring, src);
+  o.t = __shfl_sync(0xffffffffu, p.t, src);
+  o.th = __shfl_sync(0xffffffffu, p.th, src);
+  o.ts = __shfl_sync(0xffffffffu, p.ts, src);
+  o.x = __shfl_sync(0xffffffffu, p.x, src);
+  o.y = __shfl_sync(0xffffffffu, p.y, src);
+  o.z = __shfl_sync(0xffffffffu, p.z, src);
+  o.a = __shfl_sync(0xffffffffu, p.a, src);
+  o.b = __shfl_sync(0xffffffffu, p.b, src);
+  o.a0 = __shfl_sync(0xffffffffu, p.a0, src);
+  o.valid = __shfl_sync(0xffffffffu, p.valid, src);
+  o.bi = __shfl_sync(0xffffffffu, p.bi, src);
+  o.capped = __shfl_sync(0xffffffffu, p.capped, src);
+  o.pad = 0;
+  return o;
+}
+
 __device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, cplx z, cplx* f, cplx* df) {
   C3 r, rt, rth;
   surf_eval_c(S, P.ts, z, &r, &rt, &rth);
@@ -283,23 +304,20 @@ __device__ inline double sin_k_minus(int k, double x) {
 }
 
 struct Smem {
-  double *rho2, *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal, *VK, *VH, *Atab, *Dtab, *Btab;
+  double *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal, *VK, *VH, *Atab, *Dtab, *Btab;
   cplx *W0, *W1, *ph, *kc, *kk;
-  PairInfo* info;
 };
 
 __host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK) {
   const int M = Mt / 2;
   size_t d = 0;
-  d += 2 * Mt;                               // rho2, sn
+  d += Mt;                                   // sn
   d += withK ? 4 * Mt : 0;                   // tau0, bt0, hr, alph
   d += P;                                    // Acal
   d += withK ? 3 * P : 0;                    // Bcal, VK, VH
-  d += (L + 1);                              // Atab
-  d += withK ? 2 * (L + 1) : 0;              // Dtab, Btab
+  d += withK ? 3 * (L + 1) : 0;              // Atab, Dtab, Btab
   d += 4 * P;                                // W0, W1 (complex)
   d += 2 * (withK ? 3 : 2) * (2 * M + 1);    // ph, kc (, kk)
-  d += 32 * (sizeof(PairInfo) / 8);          // batch info
   return d;
 }
 
@@ -307,19 +325,16 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
   const int M = Mt / 2;
   Smem s = {};
   double* p = base;
-  s.rho2 = p; p += Mt;
   s.sn = p; p += Mt;
   if (withK) { s.tau0 = p; p += Mt; s.bt0 = p; p += Mt; s.hr = p; p += Mt; s.alph = p; p += Mt; }
   s.Acal = p; p += P;
   if (withK) { s.Bcal = p; p += P; s.VK = p; p += P; s.VH = p; p += P; }
-  s.Atab = p; p += L + 1;
-  if (withK) { s.Dtab = p; p += L + 1; s.Btab = p; p += L + 1; }
+  if (withK) { s.Atab = p; p += L + 1; s.Dtab = p; p += L + 1; s.Btab = p; p += L + 1; }
   s.W0 = (cplx*)p; p += 2 * P;
   s.W1 = (cplx*)p; p += 2 * P;
   s.ph = (cplx*)p; p += 2 * (2 * M + 1);
   s.kc = (cplx*)p; p += 2 * (2 * M + 1);
   if (withK) { s.kk = (cplx*)p; p += 2 * (2 * M + 1); }
-  s.info = (PairInfo*)p;
   return s;
 }
 
@@ -361,6 +376,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
   for (int64_t p0 = gwarp * 32; p0 < a.n_pairs; p0 += nwarps * 32) {
     const int nb = (int)min((int64_t)32, a.n_pairs - p0);
     // ---------------- decode the batch (lane per pair)
+    PairInfo mine = {};
     if (lane < nb) {
       const int64_t p = p0 + lane;
       int64_t row;
@@ -396,12 +412,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       } else if (!a.enumerate) {
         atomicAdd(a.status, 1);
       }
-      sm.info[lane] = pr;
+      mine = pr;
     }
-    __syncwarp();
+    const unsigned valid_mask = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
     // ---------------- A. grid minimiser (warp per pair)
+    double* rho2 = (double*)sm.W0;   // FFT buffer reused as Mt-length scratch in this pass
     for (int pi = 0; pi < nb; ++pi) {
-      const PairInfo pr = sm.info[pi];
+      const PairInfo pr = bcast(mine, pi);
       if (!pr.valid) continue;
       const double* rr = a.ring_r + pr.ring * 3 * Mt;
       const int i = (int)(pr.row % Mt);
@@ -417,36 +434,32 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
           const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
           r2 = yx * yx + yy * yy + yz * yz;
         }
-        sm.rho2[q] = r2;
+        rho2[q] = r2;
         bv = fmin(bv, r2);
       }
       for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
       __syncwarp();
       int bkey = 0x7fffffff;
       for (int q = lane; q < Mt; q += 32)
-        if (sm.rho2[q] <= bv * (1 + 1e-12)) {
+        if (rho2[q] <= bv * (1 + 1e-12)) {
           const int dq = q > i ? q - i : i - q;
           bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
         }
       for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
-      if (lane == 0) sm.info[pi].bi = bkey % Mt;
+      if (lane == pi) mine.bi = bkey % Mt;
       __syncwarp();
     }
     // ---------------- B. complex root and C. A_m, D_m (lane per pair)
-    if (lane < nb && sm.info[lane].valid) {
-      PairInfo pr = sm.info[lane];
-      locate_root(a.S, Mt, pr);
-      sm.info[lane].a = pr.a;
-      sm.info[lane].b = pr.b;
-      sm.info[lane].a0 = pr.a0;
-      sm.info[lane].capped = pr.capped;
+    if (lane < nb && mine.valid) {
+      locate_root(a.S, Mt, mine);
+      const PairInfo& pr = mine;
       a_modes_lane(pr.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32);
     }
     __syncwarp();
     // ---------------- D. per pair (warp)
     int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
-      const PairInfo pr = sm.info[pi];
+      const PairInfo pr = bcast(mine, pi);
       const int64_t p = p0 + pi;
       if (!pr.valid) {
         if (a.modes_out)
@@ -463,13 +476,25 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       const double qb = exp(-rb), om = -expm1(-rb);
       const bool translated = wantK && rb < kSmallB;
       // ---- D1. A_m (and D_m, B_m) of this pair; phases e^{ija}
-      for (int m = lane; m <= L; m += 32) {
-        sm.Atab[m] = scrA[m * 32 + pi];
-        if (wantK) sm.Dtab[m] = scrD[m * 32 + pi];
+      if (wantK)
+        for (int m = lane; m <= L; m += 32) {
+          sm.Atab[m] = scrA[m * 32 + pi];
+          sm.Dtab[m] = scrD[m * 32 + pi];
+        }
+      if (wantK) {
+        // e^{ija}, j = -M..M, each from its own sincos: the translated tau_3 combines phase-weighted
+        // terms that cancel, so a rotation recurrence's ulp drift would be amplified
+        for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
+      } else {
+        // single layer: e^{ija} for j = lane + 32k by steps of e^{32ia} (a few ulp), e^{-ija} = conj
+        cplx e = cexpi(lane * ra);
+        const cplx step = cexpi(32.0 * ra);
+        for (int j = lane; j <= M; j += 32) {
+          sm.ph[M + j] = e;
+          sm.ph[M - j] = conj(e);
+          e = e * step;
+        }
       }
-      // e^{ija}, j = -M..M, each from its own sincos: the translated tau_3 combines phase-weighted
-      // terms that cancel, so a rotation recurrence's ulp drift would be amplified
-      for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
       __syncwarp();
       if (wantK) {  // B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b, m = 0..2M+1
         const double shb = sinh(rb), sh2b = sinh(0.5 * rb) * sinh(0.5 * rb);
@@ -486,7 +511,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       } else {
       for (int pp = lane; pp < P; pp += 32) {
         const int dd = pp <= P / 2 ? pp : P - pp;
-        const double av = dd <= L ? sm.Atab[dd] : 0.0;
+        const double av = dd <= L ? scrA[dd * 32 + pi] : 0.0;
         double bv = 0.0;
         if (wantK && dd <= 2 * M) {
           bv = sm.Btab[dd];
@@ -528,7 +553,6 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
         const double F = sqrt(s) * rinv;
         double skr, ckr;
         sincos(a.k * rho, &skr, &ckr);
-        sm.rho2[q] = r2;
         sm.W0[q] = C(F, ckr);          // F + i cos(k rho)
         sm.sn[q] = skr * rinv;
         if (wantK) {
@@ -615,8 +639,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       if (wantS && !wantK) {
         // U = F~ C~ Acal (real) in the real part; the next valid pair's circulant A_{|d|} (real, even)
         // in the imaginary part: one transform serves both
-        int nxt = pi + 1;
-        while (nxt < nb && !sm.info[nxt].valid) ++nxt;
+        const unsigned later = valid_mask & ~((2u << pi) - 1u);   // valid pairs after pi
+        const int nxt = later ? __ffs(later) - 1 : nb;
         const bool pack = nxt < nb;
         for (int pp = lane; pp < P; pp += 32) {
           const int dd = pp <= P / 2 ? pp : P - pp;
@@ -864,11 +888,20 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
 }
 
 int pair_warps_per_block(int Mt, unsigned kernels) {
+  // the CTA shape (1, 2 or 4 warps) with the most resident warps per SM
   const bool withK = kernels & BIE_KERNEL_K;
   const int P = (withK ? 4 : 3) * Mt, L = (withK ? 4 : 3) * (Mt / 2);
   const size_t per = smem_doubles(Mt, P, L, withK) * sizeof(double);
-  int w = (int)(kSmemLimit / per);
-  return w > kMaxWarpsPerBlock ? kMaxWarpsPerBlock : w;
+  auto kern = withK ? pair_kernel<true> : pair_kernel<false>;
+  int best = 0, best_w = 0;
+  for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
+    if (per * w > kSmemLimit) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * w)) != cudaSuccess) continue;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * w, per * w) != cudaSuccess) continue;
+    if (nb * w > best_w) { best_w = nb * w; best = w; }
+  }
+  return best;
 }
 
 bie_status launch_pairs(bie_surface s, PairArgs& a) {
