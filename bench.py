@@ -247,7 +247,8 @@ def run_gpu(args):
     solve = None
     if not args.skip_solve:
         torch.cuda.synchronize()
-        Afull = bie.assemble(surf, bie.OP_S, k, out=A)
+        # exterior sound-soft problem, combined-field operator on the unweighted density (second kind)
+        Afull = bie.assemble(surf, bie.OP_CFIE | bie.UNWEIGHTED, k, out=A)
         g = bie.rhs(surf, 0, c["dirs"][0], k)
         res = {}
         for name, prec in (("fp64", 0), ("mixed_fp32_refined", 1)):
@@ -260,6 +261,7 @@ def run_gpu(args):
                 rep = {"error": str(exc)}
             res[name] = rep
         res["learned"] = None
+        res["operator"] = "I + K - i k S (combined field, unweighted density), plane wave"
         solve = res
 
     if rank == 0:

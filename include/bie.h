@@ -160,6 +160,13 @@ bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels
                                     const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
                                     double* modes_out);
 
+/* Flag for bie_assemble's op and bie_field_eval's rep: the unknown is the
+ * density itself (psi), not the weighted density psi J.  Matrix columns are
+ * multiplied by the Jacobian of the source node, so the identity of K +- I and
+ * of the combined-field operator is I instead of diag(1/J); this second-kind
+ * form is much better conditioned for iterative solvers.                      */
+#define BIE_UNWEIGHTED 0x100
+
 /* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------
  * Fill the dense N x N matrix of operator op acting on the weighted density:
  * preparation stage (Gauss-Legendre x trapezoid for every block) and

@@ -19,6 +19,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 KERNEL_S, KERNEL_K = 1, 2
 OP_S, OP_K, OP_K_PLUS_I, OP_K_MINUS_I, OP_CFIE = 0, 1, 2, 3, 4
+UNWEIGHTED = 0x100
 MAX_TERMS = 96
 
 _vp, _i64, _i32, _d, _u = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint

@@ -23,6 +23,7 @@ struct FarArgs {
   int Np, Mt;
   int64_t N;
   double h, k, wid;
+  int unweighted;
   cplx ws, wk;
   const double* pts;
   const double* nrm;
@@ -59,9 +60,9 @@ __global__ void far_fill_kernel(const FarArgs a) {
           const double f = tau0 * rinv * rinv * rinv;
           val = val + f * (a.wk * (e * C(-1.0, a.k * rho)));
         }
-        v = w * val;
+        v = (a.unweighted ? w * a.jac[col] : w) * val;
       }
-      if (col == row && a.wid != 0.0) v = v + C(a.wid / a.jac[row], 0.0);
+      if (col == row && a.wid != 0.0) v = v + C(a.unweighted ? a.wid : a.wid / a.jac[row], 0.0);
       Arow[col] = v;
     }
   }
@@ -71,7 +72,8 @@ __global__ void far_fill_kernel(const FarArgs a) {
 // A[row, block] += sS * sum_g coef W_S + sK * sum_g coef W_K   (W_K may be null)
 __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS, cplx sK,
                                  const double* __restrict__ coef, const cplx* __restrict__ WS,
-                                 const cplx* __restrict__ WK, cplx* __restrict__ A) {
+                                 const cplx* __restrict__ WK, const double* __restrict__ jcol,
+                                 cplx* __restrict__ A) {
   const int tl = blockIdx.x;            // l * Mt + i
   const int d = blockIdx.y;
   const int l = tl / Mt, i = tl % Mt;
@@ -92,7 +94,9 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS,
       if (WS) accS = accS + cf[g * 16 + n] * WS[w];
       if (WK) accK = accK + cf[g * 16 + n] * WK[w];
     }
-    Arow[e] = Arow[e] + sS * accS + sK * accK;
+    cplx add = sS * accS + sK * accK;
+    if (jcol) add = jcol[(int64_t)ip * 16 * Mt + e] * add;   // unweighted unknown: times J of the source node
+    Arow[e] = Arow[e] + add;
   }
 }
 
@@ -102,8 +106,8 @@ using namespace bie;
 
 extern "C" {
 
-bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re, double ws_im,
-                             double wk_re, double wk_im, double* A_out) {
+static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re,
+                                     double ws_im, double wk_re, double wk_im, double* A_out, bool unweighted) {
   if (!ctx || !s || !A_out) { set_error("bie_assemble_near: NULL argument"); return BIE_EINVAL; }
   if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble_near: k must be in (0, 1e6)"); return BIE_EINVAL; }
   if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
@@ -141,7 +145,7 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
       dim3 grid(16 * Mt, 3);
       near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
                                                        WS ? WS + off : nullptr, WK ? WK + off : nullptr,
-                                                       (cplx*)A_out);
+                                                       unweighted ? s->jac : nullptr, (cplx*)A_out);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");
@@ -150,7 +154,14 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
   return st;
 }
 
-bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta, double* A_out) {
+bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re, double ws_im,
+                             double wk_re, double wk_im, double* A_out) {
+  return assemble_near_impl(ctx, s, kernels, k, ws_re, ws_im, wk_re, wk_im, A_out, false);
+}
+
+bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, double eta, double* A_out) {
+  const bool unweighted = op_flags & BIE_UNWEIGHTED;
+  const int op = op_flags & ~BIE_UNWEIGHTED;
   if (!ctx || !s || !A_out) { set_error("bie_assemble: NULL argument"); return BIE_EINVAL; }
   if (op < BIE_OP_S || op > BIE_OP_CFIE) { set_error("bie_assemble: unknown operator %d", op); return BIE_EINVAL; }
   if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble: k must be in (0, 1e6)"); return BIE_EINVAL; }
@@ -173,6 +184,7 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
   fa.ws = ws;
   fa.wk = wk;
   fa.wid = wid;
+  fa.unweighted = unweighted ? 1 : 0;
   fa.pts = s->pts;
   fa.nrm = s->nrm;
   fa.jac = s->jac;
@@ -187,7 +199,7 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
   unsigned kernels = 0;
   if (ws.re != 0.0 || ws.im != 0.0) kernels |= BIE_KERNEL_S;
   if (wk.re != 0.0 || wk.im != 0.0) kernels |= BIE_KERNEL_K;
-  return bie_assemble_near(ctx, s, kernels, k, ws.re, ws.im, wk.re, wk.im, A_out);
+  return assemble_near_impl(ctx, s, kernels, k, ws.re, ws.im, wk.re, wk.im, A_out, unweighted);
 }
 
 }  // extern "C"

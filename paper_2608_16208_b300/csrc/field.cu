@@ -29,10 +29,11 @@ struct FieldArgs {
   int64_t N;
   int Mt;
   double h, k, eta;
-  int rep, far;
+  int rep, far, unweighted;
   double wgl[16];
   const double* pts;
   const double* nrm;
+  const double* jac;
   const double2* dens;
   const double* tgt;
   double2* out;
@@ -71,7 +72,7 @@ __global__ void field_kernel(const FieldArgs a) {
       }
     }
     const double2 d = a.dens[i];
-    const cplx v = w * (kern * C(d.x, d.y));
+    const cplx v = (a.unweighted ? w * a.jac[i] : w) * (kern * C(d.x, d.y));
     re += v.re;
     im += v.im;
   }
@@ -102,8 +103,9 @@ bie_status bie_rhs(bie_ctx ctx, bie_surface s, int kind, const double* param, do
   return e == cudaSuccess ? BIE_OK : cuda_fail(e, "rhs_kernel");
 }
 
-bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep, double k, double eta, const double* density,
+bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep_flags, double k, double eta, const double* density,
                           const double* pts, int64_t n, int far_field, double* out) {
+  const int rep = rep_flags & ~BIE_UNWEIGHTED;
   if (!ctx || !s || !density || !pts || !out || n < 0 || n > (1 << 30) ||
       (rep != BIE_OP_S && rep != BIE_OP_K && rep != BIE_OP_CFIE)) {
     set_error("bie_field_eval: invalid arguments");
@@ -117,6 +119,8 @@ bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep, double k, double 
   a.k = k;
   a.eta = eta;
   a.rep = rep;
+  a.unweighted = (rep_flags & BIE_UNWEIGHTED) ? 1 : 0;
+  a.jac = s->jac;
   a.far = far_field ? 1 : 0;
   for (int i = 0; i < 16; ++i) a.wgl[i] = s->gl_w[i];
   a.pts = s->pts;

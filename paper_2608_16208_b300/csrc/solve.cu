@@ -45,39 +45,50 @@ __global__ void __launch_bounds__(256) zgemv64_kernel(int64_t n, const double2* 
   }
 }
 
-// y = A32 x32 with FP32 products and FP32 accumulation; y written in FP64.
+// y = A32 x32 with FP32 products summed in FP32 over chunks of 32 terms per lane, the chunk sums
+// accumulated in FP64 (1/64 of the work in FP64, so the kernel stays bound by the FP32 matrix read);
+// y written in FP64.
 __global__ void __launch_bounds__(256) cgemv32_kernel(int64_t n, const float2* __restrict__ A,
                                                       const float2* __restrict__ x, double2* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = w; row < n; row += nw) {
+    double dre = 0.0, dim = 0.0;
     float re = 0.f, im = 0.f;
     if (n & 1) {  // rows not 16-byte aligned: plain 8-byte loads
+      int cnt = 0;
       for (int64_t c = lane; c < n; c += 32) {
         const float2 av = __ldcs(A + row * n + c), xv = __ldg(x + c);
         re = fmaf(av.x, xv.x, fmaf(-av.y, xv.y, re));
         im = fmaf(av.x, xv.y, fmaf(av.y, xv.x, im));
+        if (++cnt == 32) { dre += re; dim += im; re = im = 0.f; cnt = 0; }
       }
-      re = warp_sum_f(re);
-      im = warp_sum_f(im);
-      if (lane == 0) y[row] = make_double2(re, im);
-      continue;
+    } else {
+      const float4* a = reinterpret_cast<const float4*>(A + row * n);   // two complex entries per load
+      const float4* xv4 = reinterpret_cast<const float4*>(x);
+      const int64_t n2 = n / 2;
+      for (int64_t c0 = lane; c0 < n2; c0 += 32 * 16) {   // chunks of 16 loads (32 complex terms) per lane
+        float cr = 0.f, ci = 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int64_t c = c0 + 32 * u;
+          if (c < n2) {
+            const float4 av = __ldcs(a + c);
+            const float4 xv = __ldg(xv4 + c);
+            cr = fmaf(av.x, xv.x, fmaf(-av.y, xv.y, cr));
+            ci = fmaf(av.x, xv.y, fmaf(av.y, xv.x, ci));
+            cr = fmaf(av.z, xv.z, fmaf(-av.w, xv.w, cr));
+            ci = fmaf(av.z, xv.w, fmaf(av.w, xv.z, ci));
+          }
+        }
+        dre += cr;
+        dim += ci;
+      }
     }
-    const float4* a = reinterpret_cast<const float4*>(A + row * n);   // two complex entries per load
-    const float4* xv4 = reinterpret_cast<const float4*>(x);
-    const int64_t n2 = n / 2;
-    for (int64_t c = lane; c < n2; c += 32) {
-      const float4 av = __ldcs(a + c);
-      const float4 xv = __ldg(xv4 + c);
-      re = fmaf(av.x, xv.x, fmaf(-av.y, xv.y, re));
-      im = fmaf(av.x, xv.y, fmaf(av.y, xv.x, im));
-      re = fmaf(av.z, xv.z, fmaf(-av.w, xv.w, re));
-      im = fmaf(av.z, xv.w, fmaf(av.w, xv.z, im));
-    }
-    re = warp_sum_f(re);
-    im = warp_sum_f(im);
-    if (lane == 0) y[row] = make_double2(re, im);
+    dre = warp_sum_d(dre + re);
+    dim = warp_sum_d(dim + im);
+    if (lane == 0) y[row] = make_double2(dre, dim);
   }
 }
 
@@ -370,7 +381,8 @@ extern "C" bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const d
         if (rr <= opts->tol || total_iters >= opts->maxit) break;
         cudaMemsetAsync(dx, 0, sizeof(double2) * n, st);
         double inner_res = 0.0;
-        // inner relative tolerance: what the outer step needs, but no tighter than FP32 products allow
+        // inner relative tolerance: what the outer step needs, but not below 1e-5: FP32 products of a
+        // first-kind operator applied to rough Krylov vectors lose digits to cancellation
         const double inner_tol = std::max(1e-5, 0.5 * opts->tol / rr);
         status = S.fgmres(res, dx, inner_tol, opts->maxit - total_iters, true, &it, &inner_res);
         total_iters += it;

@@ -88,6 +88,25 @@ def test_cfie_exterior_point_source(bie, ctx, ggq):
     assert rep["iterations"] < 400
 
 
+def test_unweighted_cfie(bie, ctx, ggq):
+    # columns times the source Jacobian, identity I: same system, better conditioned
+    k, src = 4.0, [0.1, 0.1, -0.05]
+    s = bie.Surface(ctx, wl.ellipsoid(1.0, 0.8, 0.6), 6, 48, ggq)
+    Aw = bie.assemble(s, bie.OP_CFIE, k)
+    Au = bie.assemble(s, bie.OP_CFIE | bie.UNWEIGHTED, k)
+    J = torch.from_numpy(ny.boundary_nodes(wl.ellipsoid(1.0, 0.8, 0.6), 6, 48)[2]).cuda()
+    diff = (Au - Aw * J[None, :]).abs().max() / Au.abs().max()
+    assert diff.item() <= 1e-13
+    g = bie.rhs(s, 1, src, k)
+    xw, rw = bie.solve(ctx, Aw, g, tol=1e-10)
+    xu, ru = bie.solve(ctx, Au, g, tol=1e-10)
+    assert ru["iterations"] < rw["iterations"]
+    pts = wl.exterior_points(10, 3.0)
+    u = bie.field_eval(s, bie.OP_CFIE | bie.UNWEIGHTED, k, xu, pts).cpu().numpy()
+    ue = exact.point_source(k, pts, src)
+    assert np.linalg.norm(u - ue) / np.linalg.norm(ue) <= 1e-7
+
+
 def test_solver_reports_nonconvergence(bie, ctx, ggq):
     s = bie.Surface(ctx, wl.sphere(), 2, 16, ggq)
     A = bie.assemble(s, bie.OP_S, 1.0)
