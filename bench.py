@@ -264,6 +264,8 @@ def run_gpu(args):
         res["operator"] = "I + K - i k S (combined field, unweighted density), plane wave"
         solve = res
 
+    batch = None if args.batch_surfaces <= 0 else run_batch(bie, ctx, args.batch_surfaces, stream)
+
     if rank == 0:
         cpu_v, cpu_n, cpu_dt = oracle_pairs_per_second(c, seconds=15.0)
         cs = clk.summary()
@@ -283,10 +285,56 @@ def run_gpu(args):
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d near pairs of 400 seeded target rows, method mode, %.1f s" % (cpu_n, cpu_dt)},
             "solve": solve,
+            "batch": batch,
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch(bie, ctx, count, stream):
+    """Uneven batch (harmonic stars, Np in 8..32, Mth in 64..256, k in [1, 20]) in one persistent,
+    graph-captured launch, against the same surfaces run one after the other."""
+    import torch
+    specs = wl.batch_surfaces(seed=0, count=count)
+    ggq = wl.load_ggq()
+    surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
+    ks = [sp["k"] for sp in specs]
+    maxMt = max(sp["Mt"] for sp in specs)
+    slot = 1 << 20
+    W = torch.empty((1, slot, maxMt), dtype=torch.complex128, device="cuda")
+    plan = bie.Batch(ctx, surfs, ks, bie.KERNEL_S, W, slot)
+    plan.run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    # the same surfaces, one plan (one launch) each, back to back
+    singles = [bie.Batch(ctx, [sf], [k], bie.KERNEL_S, W, slot) for sf, k in zip(surfs, ks)]
+    for sp in singles:
+        sp.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sp in singles:
+        sp.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    return {"surfaces": count, "pairs": plan.pairs, "pairs_per_s": plan.pairs / (ms / 1000.0), "ms": ms,
+            "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms, "autotuned": plan.config,
+            "m_theta": sorted(sp["Mt"] for sp in specs), "panels": sorted(sp["Np"] for sp in specs),
+            "output": "ring of %d pairs x %d angles (throughput mode)" % (slot, maxMt), "cuda_graph": True}
 
 
 def run_kernel_only(n):
@@ -311,6 +359,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--batch-surfaces", type=int, default=8, help="surfaces in the batch-scheduler run (0: skip)")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: run the pair pipeline once on this many pairs of the workload and exit")
     args = ap.parse_args()

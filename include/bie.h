@@ -46,6 +46,7 @@ typedef enum {
 typedef struct bie_ctx_s* bie_ctx;
 typedef struct bie_surface_s* bie_surface;
 typedef struct bie_matrix_s* bie_matrix;
+typedef struct bie_batch_s* bie_batch;
 
 /* ---- kernels and operators ------------------------------------------------ */
 #define BIE_KERNEL_S 1u  /* e^{ik rho}/rho                      (Section 3, Eq. (Sphi:appr2)) */
@@ -166,6 +167,31 @@ bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels
  * of the combined-field operator is I instead of diag(1/J); this second-kind
  * form is much better conditioned for iterative solvers.                      */
 #define BIE_UNWEIGHTED 0x100
+
+/* ---- batch scheduler -------------------------------------------------------
+ * Many surfaces of uneven size (panels, Mth, wavenumber) in one persistent
+ * launch.  bie_batch_create builds a device-resident plan: the near pairs of
+ * every surface (all 16*Np*48*Mth enumerated (node, delta, g, theta) pairs,
+ * invalid edge pairs give zero weights) are cut into items, ordered by
+ * decreasing Mth, and an autotuner times item sizes {256, 1024, 4096} and CTA
+ * shapes {1, 2, 4 warps} on a prefix of the list and keeps the fastest.
+ * bie_batch_run resets the work counter and launches once: resident warps
+ * claim items from the counter until the list is exhausted.  It allocates
+ * nothing and can be captured in a CUDA graph (call it once before capture).
+ * Output: the Parseval weights of pair p of surface i (its enumerated index)
+ * go to row (bie_batch_offset(plan, i) + p) % slot_pairs of weights_out [dev]
+ * double2[nk][slot_pairs][max Mth] (row length = largest Mth of the batch;
+ * kernel blocks in bit order).  slot_pairs >= bie_batch_pairs(plan) keeps
+ * every row; smaller values make a bounded ring (throughput runs).
+ * The surfaces and weights_out must outlive the plan.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA, BIE_EUNSUPPORTED.                 */
+bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surface* surfs, const double* ks,
+                            unsigned kernels, double* weights_out, int64_t slot_pairs, bie_batch* out);
+bie_status bie_batch_run(bie_batch plan);
+int64_t bie_batch_pairs(bie_batch plan);
+int64_t bie_batch_offset(bie_batch plan, int i);
+void bie_batch_config(bie_batch plan, int* item_pairs, int* warps_per_block, int* blocks);
+void bie_batch_free(bie_batch plan);
 
 /* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------
  * Fill the dense N x N matrix of operator op acting on the weighted density:

@@ -203,3 +203,37 @@ def field_eval(surface, rep, k, density, points, far_field=False, eta=None):
                              _ptr(density), _ptr(pts), pts.shape[0], 1 if far_field else 0, _ptr(out)),
           "bie_field_eval")
     return out
+
+
+_sig("bie_batch_create", _i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_double), _u, _vp, _i64,
+                                ctypes.POINTER(_vp)])
+_sig("bie_batch_run", _i32, [_vp])
+_sig("bie_batch_pairs", _i64, [_vp])
+_sig("bie_batch_offset", _i64, [_vp, _i32])
+_sig("bie_batch_config", None, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)])
+_sig("bie_batch_free", None, [_vp])
+
+
+class Batch:
+    """A device-resident plan running the pair pipeline of many surfaces in one persistent launch."""
+
+    def __init__(self, ctx, surfaces, ks, kernels, weights, slot_pairs):
+        self.ctx, self.surfaces, self.weights = ctx, list(surfaces), weights
+        hs = (_vp * len(surfaces))(*[s.h for s in surfaces])
+        kk = (ctypes.c_double * len(surfaces))(*[float(k) for k in ks])
+        self.h = _vp()
+        check(lib.bie_batch_create(ctx.h, len(surfaces), hs, kk, kernels, _ptr(weights), int(slot_pairs),
+                                   ctypes.byref(self.h)), "bie_batch_create")
+        self.pairs = lib.bie_batch_pairs(self.h)
+        self.offsets = [lib.bie_batch_offset(self.h, i) for i in range(len(surfaces))]
+        a, b, c = _i32(), _i32(), _i32()
+        lib.bie_batch_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        self.config = {"item_pairs": a.value, "warps_per_block": b.value, "blocks": c.value}
+
+    def run(self):
+        check(lib.bie_batch_run(self.h), "bie_batch_run")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bie_batch_free(self.h)
+            self.h = None

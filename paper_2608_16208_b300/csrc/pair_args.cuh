@@ -28,6 +28,8 @@ struct PairArgs {
   double* modes_out;              // [p][nk][Mt+1] complex, or null
   cplx* weights_out;              // [kernel][p][Mt] complex (kernel-major when both), or null
   int64_t weights_stride;         // complex elements between the S and K weight blocks
+  int64_t out_base, out_mod;      // output slot of pair p: (out_base + p) % out_mod when out_mod > 0
+  int64_t w_ld;                   // complex elements between consecutive weight rows (Mt by default)
   int* status;
 };
 

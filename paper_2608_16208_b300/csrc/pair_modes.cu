@@ -28,6 +28,7 @@
 //      linear-convolution values.  Parseval weights: the swapped part through
 //      an inverse FFT (Nyquist split evenly), the smooth part (i sin(k rho)/rho,
 //      -i beta tau_0) by the trapezoid rule (Section 3.2).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -357,24 +358,15 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
 }
 
 // ------------------------------------------------------------------ the kernel
+// One batch of up to 32 consecutive pairs [p0, p0 + nb) of the argument set a (phases A-D).
 template <bool kWithK>
-__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const PairArgs a) {
-  extern __shared__ double smem[];
+__device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm, double* scrA, double* scrD,
+                                              int64_t p0, int nb) {
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
   const bool wantS = a.kernels & BIE_KERNEL_S;
   constexpr bool wantK = kWithK;
-  const size_t per_warp = smem_doubles(Mt, P, L, wantK);
-  Smem sm = carve(smem + per_warp * wib, Mt, P, L, wantK);
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double* scrA = a.scratch + gwarp * a.scratch_per_warp;
-  double* scrD = scrA + (int64_t)(L + 1) * 32;
   const int nk = (wantS ? 1 : 0) + (wantK ? 1 : 0);
-
-  for (int64_t p0 = gwarp * 32; p0 < a.n_pairs; p0 += nwarps * 32) {
-    const int nb = (int)min((int64_t)32, a.n_pairs - p0);
     // ---------------- decode the batch (lane per pair)
     PairInfo mine = {};
     if (lane < nb) {
@@ -460,13 +452,13 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
     int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = bcast(mine, pi);
-      const int64_t p = p0 + pi;
+      const int64_t p = a.out_mod ? (a.out_base + p0 + pi) % a.out_mod : p0 + pi;   // output slot
       if (!pr.valid) {
         if (a.modes_out)
           for (int m = lane; m < 2 * nk * (Mt + 1); m += 32) a.modes_out[p * 2 * nk * (Mt + 1) + m] = 0.0;
         if (a.weights_out)
           for (int kk = 0; kk < nk; ++kk)
-            for (int m = lane; m < Mt; m += 32) a.weights_out[kk * a.weights_stride + p * Mt + m] = C(0.0);
+            for (int m = lane; m < Mt; m += 32) a.weights_out[kk * a.weights_stride + p * a.w_ld + m] = C(0.0);
         continue;
       }
       const double ra = pr.a, rb = pr.b;
@@ -826,7 +818,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
           }
           __syncwarp();
           const cplx* Wt = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, +1);
-          cplx* wout = a.weights_out + kidx * a.weights_stride + p * Mt;
+          cplx* wout = a.weights_out + kidx * a.weights_stride + p * a.w_ld;
           for (int q = lane; q < Mt; q += 32) {
             const cplx w = Wt[q] * (1.0 / Mt);
             const double sv = (isS ? sm.sn[q] : -sm.bt0[q]) / Mt;
@@ -837,7 +829,20 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const Pair
       }
     }
     __syncwarp();
-  }
+}
+
+template <bool kWithK>
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const __grid_constant__ PairArgs a) {
+  extern __shared__ double smem[];
+  const int wib = threadIdx.x >> 5;
+  const size_t per_warp = smem_doubles(a.Mt, a.P, a.L, kWithK);
+  const Smem sm = carve(smem + per_warp * wib, a.Mt, a.P, a.L, kWithK);
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double* scrA = a.scratch + gwarp * a.scratch_per_warp;
+  double* scrD = scrA + (int64_t)(a.L + 1) * 32;
+  for (int64_t p0 = gwarp * 32; p0 < a.n_pairs; p0 += nwarps * 32)
+    process_batch<kWithK>(a, sm, scrA, scrD, p0, (int)min((int64_t)32, a.n_pairs - p0));
 }
 
 // ------------------------------------------------------------------ host side
@@ -883,6 +888,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.ring_n = s->ring_n;
   a.tw = s->tw;
   a.thg = s->thgrid;
+  a.w_ld = s->Mt;
   a.status = s->ctx->d_status;
   return a;
 }
@@ -904,6 +910,22 @@ int pair_warps_per_block(int Mt, unsigned kernels) {
   return best;
 }
 
+static bie_status ensure_rec(cudaStream_t stream, int L) {
+  const int need_rec = (int)(3.8 * L) + 64;   // Miller needs N < 3.8 L + 17 (it runs only when L b > 7)
+  if (g_res.rec_len >= need_rec) return BIE_OK;
+  std::vector<double> r = recurrence_table(need_rec);
+  cudaStreamSynchronize(stream);
+  if (g_res.rec) cudaFree(g_res.rec);
+  g_res.rec = nullptr;
+  g_res.rec_len = 0;
+  cudaError_t e = cudaMalloc((void**)&g_res.rec, sizeof(double) * r.size());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(recurrence table)");
+  e = cudaMemcpy(g_res.rec, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(recurrence table)");
+  g_res.rec_len = need_rec;
+  return BIE_OK;
+}
+
 bie_status launch_pairs(bie_surface s, PairArgs& a) {
   const bool withK = a.kernels & BIE_KERNEL_K;
   const int wpb = pair_warps_per_block(a.Mt, (unsigned)a.kernels);
@@ -920,19 +942,9 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
   const int64_t need = (a.n_pairs + 32 * wpb - 1) / (32 * wpb);
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  // recurrence table: Miller needs N < 3.8 L + 17 (it runs only when L b > 7)
-  const int need_rec = (int)(3.8 * a.L) + 64;
-  if (g_res.rec_len < need_rec) {
-    std::vector<double> r = recurrence_table(need_rec);
-    cudaStreamSynchronize(s->ctx->stream);
-    if (g_res.rec) cudaFree(g_res.rec);
-    g_res.rec = nullptr;
-    g_res.rec_len = 0;
-    e = cudaMalloc((void**)&g_res.rec, sizeof(double) * r.size());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(recurrence table)");
-    e = cudaMemcpy(g_res.rec, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(recurrence table)");
-    g_res.rec_len = need_rec;
+  {
+    const bie_status rs = ensure_rec(s->ctx->stream, a.L);
+    if (rs != BIE_OK) return rs;
   }
   a.scratch_per_warp = (int64_t)(withK ? 2 : 1) * (a.L + 1) * 32;
   const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
@@ -1062,4 +1074,225 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch (no-alloc)");
   return BIE_OK;
+}
+
+// ------------------------------------------------------------------ batch scheduler
+// Many surfaces of uneven size (panels, Mth, k) in one persistent launch: the near pairs of every
+// surface are cut into items of a fixed number of pairs, ordered by decreasing Mth (longest work
+// first), and resident warps claim items from an atomic counter until the list is exhausted.
+namespace bie {
+struct BatchItem {
+  int surf;
+  int n;
+  int64_t p0;   // first enumerated pair of the item within its surface
+};
+
+template <bool kWithK>
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
+    pair_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int n_items,
+                      int* __restrict__ counter, double* __restrict__ scratch, int64_t scratch_per_warp, int maxMt) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t per_warp = smem_doubles(maxMt, (kWithK ? 4 : 3) * maxMt, (kWithK ? 4 : 3) * (maxMt / 2), kWithK);
+  double* wbase = smem + per_warp * wib;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  double* scrA = scratch + gwarp * scratch_per_warp;
+  for (int guard = 0; guard <= n_items; ++guard) {   // each pass claims one item; bounded by the list length
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const PairArgs& a = surfs[item.surf];
+    const Smem sm = carve(wbase, a.Mt, a.P, a.L, kWithK);
+    double* scrD = scrA + (int64_t)(a.L + 1) * 32;
+    for (int q = 0; q < item.n; q += 32) process_batch<kWithK>(a, sm, scrA, scrD, item.p0 + q, min(32, item.n - q));
+  }
+}
+}  // namespace bie
+
+struct bie_batch_s {
+  bie_ctx ctx;
+  unsigned kernels;
+  bool withK;
+  int n_surf, maxMt, wpb, item_pairs, blocks, n_items;
+  size_t smem;
+  int64_t total_pairs, scratch_per_warp;
+  std::vector<bie::PairArgs> host_args;
+  std::vector<int64_t> offsets;
+  bie::PairArgs* d_args;
+  bie::BatchItem* d_items;
+  int* d_counter;
+  double* scratch;
+  float tuned_ms;
+};
+
+namespace bie {
+static std::vector<BatchItem> make_items(const bie_batch_s& b, int item_pairs) {
+  std::vector<BatchItem> items;
+  for (int sidx = 0; sidx < b.n_surf; ++sidx) {
+    const int64_t n = b.host_args[sidx].n_pairs;
+    for (int64_t p = 0; p < n; p += item_pairs)
+      items.push_back({sidx, (int)((n - p < item_pairs) ? n - p : item_pairs), p});
+  }
+  std::stable_sort(items.begin(), items.end(), [&](const BatchItem& x, const BatchItem& y) {
+    return b.host_args[x.surf].Mt > b.host_args[y.surf].Mt;
+  });
+  return items;
+}
+
+static bie_status batch_launch(bie_batch_s& b, int n_items) {
+  cudaStream_t st = b.ctx->stream;
+  cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
+  if (b.withK)
+    pair_batch_kernel<true><<<b.blocks, 32 * b.wpb, b.smem, st>>>(b.d_args, b.d_items, n_items, b.d_counter, b.scratch,
+                                                                   b.scratch_per_warp, b.maxMt);
+  else
+    pair_batch_kernel<false><<<b.blocks, 32 * b.wpb, b.smem, st>>>(b.d_args, b.d_items, n_items, b.d_counter, b.scratch,
+                                                                    b.scratch_per_warp, b.maxMt);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "pair_batch_kernel");
+}
+
+// configure grid, shared memory and scratch for a CTA shape; returns false if it does not fit
+static bool batch_configure(bie_batch_s& b, int wpb) {
+  const int P = (b.withK ? 4 : 3) * b.maxMt, L = (b.withK ? 4 : 3) * (b.maxMt / 2);
+  const size_t per = smem_doubles(b.maxMt, P, L, b.withK) * sizeof(double);
+  if (per * wpb > kSmemLimit) return false;
+  auto kern = b.withK ? pair_batch_kernel<true> : pair_batch_kernel<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb)) != cudaSuccess) return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, per * wpb) != cudaSuccess || per_sm < 1)
+    return false;
+  b.wpb = wpb;
+  b.smem = per * wpb;
+  b.blocks = b.ctx->sms * per_sm;
+  return true;
+}
+}  // namespace bie
+
+extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surface* surfs, const double* ks,
+                                       unsigned kernels, double* weights_out, int64_t slot_pairs, bie_batch* out) {
+  if (!ctx || n_surf < 1 || !surfs || !ks || !weights_out || slot_pairs < 1 || !out) {
+    set_error("bie_batch_create: invalid arguments");
+    return BIE_EINVAL;
+  }
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) { set_error("bie_batch_create: bad kernel mask"); return BIE_EINVAL; }
+  bie_batch_s* b = new bie_batch_s();
+  b->ctx = ctx;
+  b->kernels = kernels;
+  b->withK = kernels & BIE_KERNEL_K;
+  b->n_surf = n_surf;
+  b->maxMt = 0;
+  for (int i = 0; i < n_surf; ++i) {
+    if (!surfs[i] || !(ks[i] > 0) || !(ks[i] < 1e6)) { delete b; set_error("bie_batch_create: surface %d or k invalid", i); return BIE_EINVAL; }
+    b->maxMt = surfs[i]->Mt > b->maxMt ? surfs[i]->Mt : b->maxMt;
+  }
+  const int nk = (kernels & BIE_KERNEL_S ? 1 : 0) + (b->withK ? 1 : 0);
+  int64_t off = 0;
+  for (int i = 0; i < n_surf; ++i) {
+    PairArgs a = make_pair_args(surfs[i], ks[i], kernels);
+    a.enumerate = 1;
+    a.p0 = 0;
+    a.n_pairs = (int64_t)16 * surfs[i]->Np * 48 * surfs[i]->Mt;
+    a.weights_out = (cplx*)weights_out;
+    a.w_ld = b->maxMt;
+    a.out_base = off;
+    a.out_mod = slot_pairs;
+    a.weights_stride = slot_pairs * b->maxMt;
+    b->offsets.push_back(off);
+    off += a.n_pairs;
+    b->host_args.push_back(a);
+  }
+  (void)nk;
+  b->total_pairs = off;
+  bie_status st = ensure_rec(ctx->stream, (b->withK ? 4 : 3) * (b->maxMt / 2));
+  if (st != BIE_OK) { delete b; return st; }
+  for (auto& a : b->host_args) {
+    a.rec = g_res.rec;
+    a.rec_len = g_res.rec_len;
+  }
+  cudaError_t e = cudaMalloc((void**)&b->d_args, sizeof(PairArgs) * n_surf);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch)"); }
+  e = cudaMemcpy(b->d_args, b->host_args.data(), sizeof(PairArgs) * n_surf, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "cudaMemcpy(batch args)"); }
+  b->scratch_per_warp = (int64_t)(b->withK ? 2 : 1) * ((b->withK ? 4 : 3) * (b->maxMt / 2) + 1) * 32;
+  // ---- autotuner: item size x CTA shape, timed on a prefix of the work list (about 1/16 of the pairs)
+  const int item_cands[3] = {256, 1024, 4096};
+  const int wpb_cands[3] = {1, 2, 4};
+  float best = 1e30f;
+  int best_item = 1024, best_wpb = 0;
+  b->d_items = nullptr;
+  b->scratch = nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  size_t max_scratch = 0;
+  for (int wi = 0; wi < 3; ++wi) {
+    if (!batch_configure(*b, wpb_cands[wi])) continue;
+    max_scratch = std::max(max_scratch, sizeof(double) * (size_t)b->scratch_per_warp * b->blocks * b->wpb);
+  }
+  e = cudaMalloc((void**)&b->scratch, max_scratch);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return cuda_fail(e, "cudaMalloc(batch scratch)"); }
+  for (int ii = 0; ii < 3; ++ii) {
+    std::vector<BatchItem> items = make_items(*b, item_cands[ii]);
+    if (b->d_items) cudaFree(b->d_items);
+    e = cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return cuda_fail(e, "batch items"); }
+    const int prefix = (int)std::max<size_t>(1, items.size() / 16);
+    for (int wi = 0; wi < 3; ++wi) {
+      if (!batch_configure(*b, wpb_cands[wi])) continue;
+      cudaEventRecord(e0, ctx->stream);
+      st = batch_launch(*b, prefix);
+      cudaEventRecord(e1, ctx->stream);
+      if (st != BIE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return st; }
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_item = item_cands[ii]; best_wpb = wpb_cands[wi]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!best_wpb || !batch_configure(*b, best_wpb)) { bie_batch_free(b); set_error("bie_batch_create: no CTA shape fits"); return BIE_EUNSUPPORTED; }
+  std::vector<BatchItem> items = make_items(*b, best_item);
+  cudaFree(b->d_items);
+  e = cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items.size());
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "batch items"); }
+  b->n_items = (int)items.size();
+  b->item_pairs = best_item;
+  b->tuned_ms = best;
+  *out = b;
+  return BIE_OK;
+}
+
+extern "C" bie_status bie_batch_run(bie_batch b) {
+  if (!b) { set_error("bie_batch_run: NULL plan"); return BIE_EINVAL; }
+  return batch_launch(*b, b->n_items);
+}
+
+extern "C" int64_t bie_batch_pairs(bie_batch b) { return b ? b->total_pairs : 0; }
+
+extern "C" int64_t bie_batch_offset(bie_batch b, int i) {
+  return (b && i >= 0 && i < b->n_surf) ? b->offsets[i] : -1;
+}
+
+extern "C" void bie_batch_config(bie_batch b, int* item_pairs, int* warps_per_block, int* blocks) {
+  if (!b) return;
+  if (item_pairs) *item_pairs = b->item_pairs;
+  if (warps_per_block) *warps_per_block = b->wpb;
+  if (blocks) *blocks = b->blocks;
+}
+
+extern "C" void bie_batch_free(bie_batch b) {
+  if (!b) return;
+  cudaFree(b->d_args);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  cudaFree(b->scratch);
+  delete b;
 }
