@@ -296,6 +296,8 @@ def run_batch(bie, ctx, count, stream):
     """Uneven batch (harmonic stars, Np in 8..32, Mth in 64..256, k in [1, 20]) in one persistent,
     graph-captured launch, against the same surfaces run one after the other."""
     import torch
+    stream = torch.cuda.Stream()              # graph capture needs a non-default stream
+    ctx = bie.Context(stream)
     specs = wl.batch_surfaces(seed=0, count=count)
     ggq = wl.load_ggq()
     surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
@@ -303,6 +305,7 @@ def run_batch(bie, ctx, count, stream):
     maxMt = max(sp["Mt"] for sp in specs)
     slot = 1 << 20
     W = torch.empty((1, slot, maxMt), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
     plan = bie.Batch(ctx, surfs, ks, bie.KERNEL_S, W, slot)
     plan.run()
     torch.cuda.synchronize()
@@ -313,9 +316,10 @@ def run_batch(bie, ctx, count, stream):
     times = []
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
+        with torch.cuda.stream(stream):       # replay() launches on the current stream
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = min(times)

@@ -1141,8 +1141,23 @@ static std::vector<BatchItem> make_items(const bie_batch_s& b, int item_pairs) {
   return items;
 }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared by every plan:
+// it only grows, so a plan configured earlier (or captured in a graph) keeps launching.
+static int g_batch_smem_attr[2] = {0, 0};
+static bie_status batch_smem_attr(bool withK, size_t smem) {
+  int& cur = g_batch_smem_attr[withK ? 1 : 0];
+  if ((int)smem <= cur) return BIE_OK;
+  auto kern = withK ? pair_batch_kernel<true> : pair_batch_kernel<false>;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_batch_kernel)");
+  cur = (int)smem;
+  return BIE_OK;
+}
+
 static bie_status batch_launch(bie_batch_s& b, int n_items) {
   cudaStream_t st = b.ctx->stream;
+  const bie_status as = batch_smem_attr(b.withK, b.smem);
+  if (as != BIE_OK) return as;
   cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
   if (b.withK)
@@ -1161,7 +1176,7 @@ static bool batch_configure(bie_batch_s& b, int wpb) {
   const size_t per = smem_doubles(b.maxMt, P, L, b.withK) * sizeof(double);
   if (per * wpb > kSmemLimit) return false;
   auto kern = b.withK ? pair_batch_kernel<true> : pair_batch_kernel<false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb)) != cudaSuccess) return false;
+  if (batch_smem_attr(b.withK, per * wpb) != BIE_OK) return false;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, per * wpb) != cudaSuccess || per_sm < 1)
     return false;
