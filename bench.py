@@ -33,6 +33,10 @@ WORKLOAD = "ellipsoid_np16_m128_k10"
 METRIC = "kernel-mode pairs/s (correction stage, S kernel, FP64)"
 UNIT = "pairs/s"
 FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (profiles/fp64_peak_probe.md)
+# DRAM bytes (read + write) per pair of the pair kernel, from one ncu capture of 75,776 pairs of this
+# workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md), valid only for the kernel source it was
+# taken on: the report carries it while the sources hash to the same value, and null otherwise.
+PAIR_TRAFFIC = {"bytes_per_pair": (68.090624e6 + 292.715776e6) / 75776, "sources": "be4bc295f36c51fe"}
 
 
 def algorithmic_flops_per_pair(Mt):
@@ -147,6 +151,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def pair_kernel_sources_hash():
+    import glob
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2608_16208_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "pair_modes.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def near_launches(Np, Mt, nk):
+    """Kernel launches of one near-correction pass: the pair pipeline once per group of panels whose
+    weights fit 4 GiB, and the near-band fill once per panel."""
+    per_panel = 16 * (16 * 48 * Mt) * Mt * nk
+    group = max(1, min(Np, (4 << 30) // per_panel))
+    return -(-Np // group) + Np
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -196,7 +219,7 @@ def run_gpu(args):
         step_ms = float(t.item())
     pairs = surf.near_pairs
     value = world * pairs / (step_ms / 1000.0)
-    launches_per_step = 2 * Np
+    launches_per_step = near_launches(Np, Mt, 1)
 
     # dominant kernel: the pair pipeline over every near pair of the surface in one launch (the
     # launch size of a step), timed with events on the launching stream
@@ -219,6 +242,8 @@ def run_gpu(args):
     pk_pairs = rows_all.numel()
     del modes, rows_all, srcs_all, panel, keep
     fl = algorithmic_flops_per_pair(Mt)
+    traffic = (PAIR_TRAFFIC["bytes_per_pair"] * pk_pairs
+               if pair_kernel_sources_hash() == PAIR_TRAFFIC["sources"] else None)
     achieved_gflops = fl * pk_pairs / (pk_ms / 1000.0) / 1e9
     step_gflops = fl * pairs / (step_ms / 1000.0) / 1e9
 
@@ -277,8 +302,10 @@ def run_gpu(args):
             "clocks": cs,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": None,
-                         "kernel": "pair_s_kernel", "peak_source": "measured FP64 FMA probe",
+                         "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
+                         "kernel": "pair_kernel<S>", "peak_source": "measured FP64 FMA probe",
+                         "traffic_source": "ncu capture of 75,776 pairs, scaled to the %d pairs of a launch" % pk_pairs,
+                         "launch_ms": pk_ms,
                          "flops_per_pair": fl, "step_gflops": step_gflops},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": float(np.median(e2e_ms))},
