@@ -212,15 +212,93 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
 bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
                              double ws_re, double ws_im, double wk_re, double wk_im, double* A_out);
 
+/* ---- block-diagonal preconditioner ------------------------------------------
+ * LU factors, with partial pivoting, of the n / block diagonal blocks
+ * A[b block : (b+1) block, same] of the system matrix.  With block = 16 Mth
+ * a block is one panel's self interaction (16 Gauss-Legendre rings x Mth
+ * samples, every self-panel GGQ correction of Section 3.4).  Factors are FP32
+ * complex (an approximate inverse; FGMRES keeps the outer residual in FP64).
+ *   A [dev] double2[n][n] row-major (read once; not kept).
+ *   32 <= block <= 4096, block divides n.  Holds n * block float2 of device
+ *   memory until bie_blockdiag_free.  Synchronises the ctx stream.
+ * bie_blockdiag_apply: z = B^{-1} r for nv vectors, r, z [dev] double2[nv][n],
+ *   z must not alias r; asynchronous on the ctx stream.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA, BIE_ENAN (a block has a zero
+ * pivot column; the message names the block).                               */
+typedef struct bie_blockdiag_s* bie_blockdiag;
+bie_status bie_blockdiag_create(bie_ctx ctx, int64_t n, const double* A, int block, bie_blockdiag* out);
+bie_status bie_blockdiag_apply(bie_blockdiag P, const double* r, int nv, double* z);
+int64_t bie_blockdiag_size(bie_blockdiag P);
+void bie_blockdiag_free(bie_blockdiag P);
+
+/* ---- learned preconditioner ---------------------------------------------------
+ * A 4-layer convolutional network on the (t, theta) grid of the unknowns
+ * (t = panel * 16 + node rows, Mth columns): 3x3 convolutions
+ * 4 -> 32 -> 32 -> 32 -> 2, dilations 1, 2, 4, 1, ReLU after the first three,
+ * theta periodic, t zero-padded.  For a residual r its input features are
+ * Re r / s, Im r / s, J / mean(J), k / 25 with s = rms(r); the preconditioner
+ * is z = B^{-1} r + s (o_0 + i o_1) (B^{-1}: the block-diagonal factors, or 0).
+ * Parameters: float[BIE_NET_PARAMS], per layer W[cout][cin][3][3] then
+ * bias[cout].  The FP32 master copy is trained (Adam); every pass uses its
+ * BF16 rounding with FP32 accumulation.
+ * Feature / output tensors: [dev] float[B][C][nt][mt], C = 4 in, 2 out.
+ *
+ * bie_net_create: params [host] (NULL: seeded He-uniform hidden layers, zero
+ *   output layer, zero biases, so that z = B^{-1} r at start).
+ * bie_net_forward: y = net(x).
+ * bie_net_backward: gradients of sum(gy * net(x)) w.r.t. the parameters
+ *   (gparams [dev] float[BIE_NET_PARAMS]) and x (gx, may be NULL).
+ * bie_train_set_create: a training system: the surface (grid, J), k, the
+ *   system matrix A [dev] double2[N][N] (an FP32 copy is kept, 8 N^2 bytes)
+ *   and the block preconditioner used as the base (may be NULL).
+ * bie_net_loss_grad: L = (1/nv) sum_v ||A z_v - r_v||^2 / ||r_v||^2 for
+ *   r [dev] float2[nv][N] (nv <= 16) and its parameter gradient (gparams
+ *   [dev], may be NULL); loss [host].
+ * bie_net_train: opts->steps Adam steps; step i uses set i mod n_sets and a
+ *   batch of residuals drawn from splitmix64 (seed, step): half complex
+ *   white noise, half A x with white x.  loss_history [host] float[steps]
+ *   (may be NULL).  Synchronises the ctx stream.
+ * bie_net_precond_apply: z = B^{-1} v + s net(features(v)) for nv <= 16
+ *   vectors v, z [dev] double2[nv][N] of the surface (block may be NULL).
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.                                  */
+#define BIE_NET_PARAMS 20258
+typedef struct bie_net_s* bie_net;
+typedef struct bie_train_set_s* bie_train_set;
+typedef struct {
+  int steps;
+  int batch;         /* 2 .. 16 */
+  float lr;
+  float beta1, beta2, eps;
+  uint64_t seed;
+} bie_train_opts;
+bie_status bie_net_create(bie_ctx ctx, const float* params, uint64_t seed, bie_net* out);
+bie_status bie_net_get_params(bie_net net, float* params);
+void bie_net_free(bie_net net);
+bie_status bie_net_forward(bie_net net, int B, int nt, int mt, const float* x, float* y);
+bie_status bie_net_backward(bie_net net, int B, int nt, int mt, const float* x, const float* gy,
+                            float* gparams, float* gx);
+bie_status bie_train_set_create(bie_ctx ctx, bie_surface s, double k, const double* A,
+                                bie_blockdiag block, bie_train_set* out);
+void bie_train_set_free(bie_train_set ts);
+bie_status bie_net_loss_grad(bie_net net, bie_train_set ts, const float* r, int nv, float* gparams,
+                             float* loss);
+bie_status bie_net_train(bie_net net, const bie_train_set* sets, int n_sets, const bie_train_opts* opts,
+                         float* loss_history);
+bie_status bie_net_precond_apply(bie_net net, bie_blockdiag block, bie_surface s, double k,
+                                 const double* v, int nv, double* z);
+
 /* ---- dense solve -------------------------------------------------------------
- * Restarted FGMRES (right preconditioned, modified Gram-Schmidt with
+ * Restarted FGMRES (right preconditioned, classical Gram-Schmidt with
  * re-orthogonalisation) on A x = b for nrhs right-hand sides, one after the
  * other, until ||b - A x|| <= tol ||b||.
  *   A    [dev] double2[N][N] row-major;  rhs [dev] double2[nrhs][N];
  *   x    [dev] double2[nrhs][N] (initial guess in, solution out).
  *   prec 0 = FP64 matvec, 1 = FP32-stored matrix inside FGMRES with FP64
  *        iterative refinement (outer residuals in FP64).
- *   precond must be 0 (no preconditioner) in this build.
+ *   precond 0 = none; 1 = block-diagonal (block); 2 = learned (net on the
+ *        grid of surface, wavenumber k, on top of block if it is not NULL).
+ *        With precond = 2 a solve that does not converge or meets a NaN is
+ *        run again with precond = 1 from the initial guess (fallback_used).
  * Uses device work memory of (2 restart + 4) N double2 (+ N*N float2 for
  * prec = 1), allocated stream-ordered and freed before return.
  * report[host] (may be NULL): iterations, final relative residual, flags.
@@ -231,12 +309,17 @@ typedef struct {
   int maxit;
   int prec;
   int precond;
+  bie_blockdiag block;   /* precond 1, optional base for 2 */
+  bie_net net;           /* precond 2 */
+  bie_surface surface;   /* precond 2: the grid and Jacobians of the unknowns */
+  double k;              /* precond 2: wavenumber feature */
 } bie_solve_opts;
 typedef struct {
   int iterations;        /* total inner iterations over all right-hand sides */
   int refinements;       /* outer FP64 refinement steps (prec = 1)            */
   double rel_residual;   /* max over right-hand sides, FP64 residual          */
   double seconds;        /* wall time of the call                             */
+  int fallback_used;     /* precond = 2 fell back to the block preconditioner */
 } bie_solve_report;
 bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const double* rhs, int nrhs,
                      double* x, const bie_solve_opts* opts, bie_solve_report* report);

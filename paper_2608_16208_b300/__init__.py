@@ -37,12 +37,24 @@ class QuadTables(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("prec", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("precond", ctypes.c_int), ("block", ctypes.c_void_p),
+                ("net", ctypes.c_void_p), ("surface", ctypes.c_void_p), ("k", ctypes.c_double)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("fallback_used", ctypes.c_int)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+NET_PARAMS = 20258
+PRECOND_NONE, PRECOND_BLOCK, PRECOND_LEARNED = 0, 1, 2
 
 
 def _sig(name, res, args):
@@ -128,6 +140,24 @@ class Surface:
         self.N = lib.bie_surface_unknowns(self.h)
         self.near_pairs = lib.bie_surface_near_pairs(self.h)
 
+    def _copy(self, ptr, shape):
+        """Copy of a library-owned device array of doubles (the view goes through the CUDA array interface)."""
+        view = type("_DeviceDoubles", (), {})()
+        view.__cuda_array_interface__ = {"shape": shape, "typestr": "<f8", "data": (ptr, False), "version": 2}
+        return torch.as_tensor(view, device="cuda").clone()
+
+    def points(self):
+        """Node positions [N, 3]."""
+        return self._copy(lib.bie_surface_points(self.h), (self.N, 3))
+
+    def normals(self):
+        """Unit normals [N, 3]."""
+        return self._copy(lib.bie_surface_normals(self.h), (self.N, 3))
+
+    def jacobians(self):
+        """Surface Jacobians J = |r_t x r_theta| [N]."""
+        return self._copy(lib.bie_surface_jacobians(self.h), (self.N,))
+
     def __del__(self):
         if getattr(self, "h", None):
             lib.bie_surface_free(self.h)
@@ -170,20 +200,139 @@ def assemble_near(surface, kernels, k, A, ws=1.0, wk=0.0):
     return A
 
 
-def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0):
-    """FGMRES solve of A x = b (b: [N] or [nrhs, N]); returns (x, report dict)."""
+def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,
+          surface=None, k=0.0):
+    """FGMRES solve of A x = b (b: [N] or [nrhs, N]); returns (x, report dict).
+
+    precond: 0 none, 1 block-diagonal (block), 2 learned (net on the grid of surface, wavenumber k,
+    on top of block if given; falls back to block when it does not converge)."""
     n = A.shape[0]
     bb = b.reshape(-1, n).contiguous()
     nrhs = bb.shape[0]
     if x is None:
         x = torch.zeros_like(bb)
-    o = SolveOpts(tol, restart, maxit, prec, 0)
+    o = SolveOpts(tol, restart, maxit, prec, precond, block.h if block is not None else None,
+                  net.h if net is not None else None, surface.h if surface is not None else None, float(k))
     r = SolveReport()
     st = lib.bie_solve(ctx.h, n, _ptr(A), _ptr(bb), nrhs, _ptr(x), ctypes.byref(o), ctypes.byref(r))
     rep = {"iterations": r.iterations, "refinements": r.refinements, "rel_residual": r.rel_residual,
-           "seconds": r.seconds, "status": st}
+           "seconds": r.seconds, "fallback_used": r.fallback_used, "status": st}
     check(st, "bie_solve")
     return x.reshape(b.shape), rep
+
+
+_sig("bie_blockdiag_create", _i32, [_vp, _i64, _vp, _i32, ctypes.POINTER(_vp)])
+_sig("bie_blockdiag_apply", _i32, [_vp, _vp, _i32, _vp])
+_sig("bie_blockdiag_size", _i64, [_vp])
+_sig("bie_blockdiag_free", None, [_vp])
+_sig("bie_net_create", _i32, [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(_vp)])
+_sig("bie_net_get_params", _i32, [_vp, _vp])
+_sig("bie_net_free", None, [_vp])
+_sig("bie_net_forward", _i32, [_vp, _i32, _i32, _i32, _vp, _vp])
+_sig("bie_net_backward", _i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp])
+_sig("bie_train_set_create", _i32, [_vp, _vp, _d, _vp, _vp, ctypes.POINTER(_vp)])
+_sig("bie_train_set_free", None, [_vp])
+_sig("bie_net_loss_grad", _i32, [_vp, _vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_float)])
+_sig("bie_net_train", _i32, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(TrainOpts), _vp])
+_sig("bie_net_precond_apply", _i32, [_vp, _vp, _vp, _d, _vp, _i32, _vp])
+
+
+class BlockDiag:
+    """LU factors (FP32 complex, partial pivoting) of the diagonal blocks of A."""
+
+    def __init__(self, ctx, A, block):
+        self.ctx = ctx
+        self.h = _vp()
+        check(lib.bie_blockdiag_create(ctx.h, A.shape[0], _ptr(A), int(block), ctypes.byref(self.h)),
+              "bie_blockdiag_create")
+
+    def apply(self, r, out=None):
+        rr = r.reshape(-1, r.shape[-1]).contiguous()
+        z = torch.empty_like(rr) if out is None else out
+        check(lib.bie_blockdiag_apply(self.h, _ptr(rr), rr.shape[0], _ptr(z)), "bie_blockdiag_apply")
+        return z.reshape(r.shape)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bie_blockdiag_free(self.h)
+            self.h = None
+
+
+class Net:
+    """The learned preconditioner's network (4 convolutional layers, width 32)."""
+
+    def __init__(self, ctx, params=None, seed=0):
+        self.ctx = ctx
+        self.h = _vp()
+        hp = None
+        if params is not None:
+            self._init = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+            hp = self._init.ctypes.data_as(_vp)
+        check(lib.bie_net_create(ctx.h, hp, int(seed), ctypes.byref(self.h)), "bie_net_create")
+
+    def params(self):
+        out = np.empty(NET_PARAMS, dtype=np.float32)
+        check(lib.bie_net_get_params(self.h, out.ctypes.data_as(_vp)), "bie_net_get_params")
+        return out
+
+    def forward(self, x):
+        B, _, nt, mt = x.shape
+        x = x.contiguous()
+        y = torch.empty((B, 2, nt, mt), dtype=torch.float32, device=x.device)
+        check(lib.bie_net_forward(self.h, B, nt, mt, _ptr(x), _ptr(y)), "bie_net_forward")
+        return y
+
+    def backward(self, x, gy, want_gx=True):
+        B, _, nt, mt = x.shape
+        x, gy = x.contiguous(), gy.contiguous()
+        gp = torch.empty(NET_PARAMS, dtype=torch.float32, device=x.device)
+        gx = torch.empty_like(x) if want_gx else None
+        check(lib.bie_net_backward(self.h, B, nt, mt, _ptr(x), _ptr(gy), _ptr(gp),
+                                   _ptr(gx) if gx is not None else None), "bie_net_backward")
+        return gp, gx
+
+    def loss_grad(self, tset, r):
+        """Training loss of residuals r (complex64 [nv, N]) and its parameter gradient."""
+        r = r.contiguous()
+        gp = torch.empty(NET_PARAMS, dtype=torch.float32, device=r.device)
+        loss = ctypes.c_float()
+        check(lib.bie_net_loss_grad(self.h, tset.h, _ptr(r), r.shape[0], _ptr(gp), ctypes.byref(loss)),
+              "bie_net_loss_grad")
+        return float(loss.value), gp
+
+    def train(self, sets, steps, batch=16, lr=1e-3, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
+        hs = (_vp * len(sets))(*[t.h for t in sets])
+        o = TrainOpts(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(seed))
+        hist = np.empty(int(steps), dtype=np.float32)
+        check(lib.bie_net_train(self.h, hs, len(sets), ctypes.byref(o), hist.ctypes.data_as(_vp)), "bie_net_train")
+        return hist
+
+    def precond_apply(self, surface, k, v, block=None):
+        vv = v.reshape(-1, v.shape[-1]).contiguous()
+        z = torch.empty_like(vv)
+        check(lib.bie_net_precond_apply(self.h, block.h if block is not None else None, surface.h, float(k),
+                                        _ptr(vv), vv.shape[0], _ptr(z)), "bie_net_precond_apply")
+        return z.reshape(v.shape)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bie_net_free(self.h)
+            self.h = None
+
+
+class TrainSet:
+    """A training system for the network: surface grid, k, FP32 copy of A, block preconditioner."""
+
+    def __init__(self, ctx, surface, k, A, block=None):
+        self.ctx, self.surface, self.block = ctx, surface, block
+        self.h = _vp()
+        check(lib.bie_train_set_create(ctx.h, surface.h, float(k), _ptr(A), block.h if block is not None else None,
+                                       ctypes.byref(self.h)), "bie_train_set_create")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bie_train_set_free(self.h)
+            self.h = None
 
 
 def rhs(surface, kind, param, k, out=None):

@@ -341,7 +341,16 @@ struct bie_surface_s {
   bie::GL16 gl01;              // the same rule mapped to [0, 1]
 };
 
+struct bie_net_infer_s;
+
 namespace bie {
 void set_error(const char* fmt, ...);
 bie_status cuda_fail(cudaError_t e, const char* where);
+// preconditioners (blockdiag.cu, precond_net.cu)
+bie_status blockdiag_apply_dev(bie_blockdiag P, const double2* r, int nv, double2* z);
+bie_status blockdiag_apply_f32(bie_blockdiag P, const float2* r, int nv, float2* z);
+bie_net_infer_s* net_infer_new();
+void net_infer_free(bie_net_infer_s* I);
+bie_status net_precond_apply_dev(bie_net net, bie_net_infer_s* I, bie_blockdiag block, bie_surface s, double k,
+                                 const double2* v, int nv, double2* z);
 }  // namespace bie

@@ -208,9 +208,18 @@ struct Solver {
     return e == cudaSuccess ? BIE_OK : cuda_fail(e, "matvec");
   }
 
-  // identity preconditioner (the flexible slot Z_j = M^{-1} V_j is kept for a future M)
-  void precond(const double2* v, double2* z) {
-    cudaMemcpyAsync(z, v, sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+  // right preconditioner, flexible slot Z_j = M(V_j): none, block-diagonal, or learned (+ block)
+  int pkind = 0;
+  bie_blockdiag block = nullptr;
+  bie_net net = nullptr;
+  bie_surface surface = nullptr;
+  double k = 0.0;
+  bie_net_infer_s* infer = nullptr;
+  bie_status precond(const double2* v, double2* z) {
+    if (pkind == 1) return blockdiag_apply_dev(block, v, 1, z);
+    if (pkind == 2) return net_precond_apply_dev(net, infer, block, surface, k, v, 1, z);
+    const cudaError_t e = cudaMemcpyAsync(z, v, sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+    return e == cudaSuccess ? BIE_OK : cuda_fail(e, "precond");
   }
 
   // h[0..J) = V[0..J)^H w  (copied to the host)
@@ -257,7 +266,8 @@ struct Solver {
       g[0] = beta;
       int jdone = 0;
       for (int j = 0; j < m && total < maxit; ++j) {
-        precond(V + (int64_t)j * n, Z + (int64_t)j * n);
+        s = precond(V + (int64_t)j * n, Z + (int64_t)j * n);
+        if (s) return s;
         s = matvec(Z + (int64_t)j * n, w, low);
         if (s) return s;
         // classical Gram-Schmidt, twice
@@ -319,13 +329,28 @@ extern "C" bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const d
   const auto t0 = std::chrono::steady_clock::now();
   if (!ctx || !A || !rhs || !x || n <= 0 || nrhs <= 0 || !opts) { set_error("bie_solve: invalid arguments"); return BIE_EINVAL; }
   if (!(opts->tol > 0) || opts->restart < 1 || opts->restart > 1000 || opts->maxit < 1 || opts->prec < 0 ||
-      opts->prec > 1 || opts->precond != 0) {
-    set_error("bie_solve: invalid options (precond must be 0 in this build)");
+      opts->prec > 1 || opts->precond < 0 || opts->precond > 2) {
+    set_error("bie_solve: invalid options");
+    return BIE_EINVAL;
+  }
+  if (opts->precond == 1 && (!opts->block || bie_blockdiag_size(opts->block) != n)) {
+    set_error("bie_solve: precond = 1 needs a block preconditioner of size n");
+    return BIE_EINVAL;
+  }
+  if (opts->precond == 2 && (!opts->net || !opts->surface || opts->surface->N != n || !(opts->k > 0) ||
+                             (opts->block && bie_blockdiag_size(opts->block) != n))) {
+    set_error("bie_solve: precond = 2 needs a network, the surface of the unknowns and k > 0");
     return BIE_EINVAL;
   }
   Solver S;
   S.ctx = ctx;
   S.n = n;
+  S.pkind = opts->precond;
+  S.block = opts->block;
+  S.net = opts->net;
+  S.surface = opts->surface;
+  S.k = opts->k;
+  if (S.pkind == 2) S.infer = net_infer_new();
   S.m = opts->restart;
   S.A64 = (const double2*)A;
   S.dot_blocks = ctx->sms * 2;
@@ -362,13 +387,19 @@ extern "C" bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const d
     e = cudaGetLastError();
     if (e != cudaSuccess) status = cuda_fail(e, "to_f32");
   }
+  int fallback = 0, budget0 = 0;
+  double2* x0 = nullptr;
+  if (S.pkind == 2 && opts->block) alloc((void**)&x0, sizeof(double2) * n);
+  if (e != cudaSuccess && status == BIE_OK) status = cuda_fail(e, "bie_solve allocation");
   for (int c = 0; c < nrhs && status == BIE_OK; ++c) {
     const double2* b = (const double2*)rhs + (int64_t)c * n;
     double2* xc = (double2*)x + (int64_t)c * n;
+    if (x0) cudaMemcpyAsync(x0, xc, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st);
+  retry:
     int it = 0;
     double rr = 0.0;
     if (opts->prec == 0) {
-      status = S.fgmres(b, xc, opts->tol, opts->maxit - total_iters, false, &it, &rr);
+      status = S.fgmres(b, xc, opts->tol, opts->maxit - (total_iters - budget0), false, &it, &rr);
       total_iters += it;
     } else {
       const double bnorm = S.norm(b);
@@ -378,21 +409,30 @@ extern "C" bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const d
         sub_kernel<<<ctx->sms * 4, 256, 0, st>>>(n, b, S.tmp, res);
         rr = bnorm > 0 ? S.norm(res) / bnorm : 0.0;
         if (!(rr == rr)) { status = BIE_ENAN; break; }
-        if (rr <= opts->tol || total_iters >= opts->maxit) break;
+        if (rr <= opts->tol || total_iters - budget0 >= opts->maxit) break;
         cudaMemsetAsync(dx, 0, sizeof(double2) * n, st);
         double inner_res = 0.0;
         // inner relative tolerance: what the outer step needs, but not below 1e-5: FP32 products of a
         // first-kind operator applied to rough Krylov vectors lose digits to cancellation
         const double inner_tol = std::max(1e-5, 0.5 * opts->tol / rr);
-        status = S.fgmres(res, dx, inner_tol, opts->maxit - total_iters, true, &it, &inner_res);
+        status = S.fgmres(res, dx, inner_tol, opts->maxit - (total_iters - budget0), true, &it, &inner_res);
         total_iters += it;
         ++refinements;
         if (status) break;
         add_kernel<<<ctx->sms * 4, 256, 0, st>>>(n, dx, xc);
       }
     }
-    worst = std::max(worst, rr);
     if (status == BIE_OK && !(rr <= opts->tol)) status = BIE_ENOCONV;
+    // learned preconditioner gave no convergence (or a NaN): the block-diagonal one takes over
+    if ((status == BIE_ENOCONV || status == BIE_ENAN) && S.pkind == 2 && x0) {
+      S.pkind = 1;
+      fallback = 1;
+      budget0 = total_iters;  // the fallback solve gets a fresh iteration budget
+      status = BIE_OK;
+      cudaMemcpyAsync(xc, x0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st);
+      goto retry;
+    }
+    worst = std::max(worst, rr);
   }
   for (void* p : owned) cudaFreeAsync(p, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
@@ -402,7 +442,9 @@ extern "C" bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const d
     report->refinements = refinements;
     report->rel_residual = worst;
     report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    report->fallback_used = fallback;
   }
+  net_infer_free(S.infer);
   if (status == BIE_ENOCONV) set_error("bie_solve: tolerance not reached within maxit");
   if (status == BIE_ENAN) set_error("bie_solve: NaN in the residual");
   return status;

@@ -196,3 +196,10 @@ def exterior_points(n, radius, seed=0, stream=5):
     r = np.sqrt(1 - z * z)
     ph = np.pi * (3 - math.sqrt(5)) * i + phase
     return radius * np.stack([r * np.cos(ph), r * np.sin(ph), z], -1)
+
+
+def random_complex(shape, seed, stream):
+    """Complex normal array (E|z|^2 = 1) from numpy's PCG64 seeded by (seed, stream); for large
+    synthetic test matrices, where the per-value splitmix64 stream above is too slow in Python."""
+    g = np.random.default_rng([int(seed), int(stream)])
+    return (g.standard_normal(shape) + 1j * g.standard_normal(shape)) / np.sqrt(2.0)
