@@ -285,8 +285,8 @@ def run_gpu(args):
             except bie.BieError as exc:
                 rep = {"error": str(exc)}
             res[name] = rep
-        res["learned"] = None
         res["operator"] = "I + K - i k S (combined field, unweighted density), plane wave"
+        res["learned"] = run_learned(bie) if args.learned else None
         solve = res
 
     batch = None if args.batch_surfaces <= 0 else run_batch(bie, ctx, args.batch_surfaces, stream)
@@ -297,7 +297,7 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64+f32x2", "data": "synthetic",
             "config": config_json(c, {"parallelism": "replicas" if world > 1 else "single"}),
             "clocks": cs,
             "gpu_launches": launches_per_step * args.steps,
@@ -368,6 +368,77 @@ def run_batch(bie, ctx, count, stream):
             "output": "ring of %d pairs x %d angles (throughput mode)" % (slot, maxMt), "cuda_graph": True}
 
 
+def learned_family(seed, i):
+    """System i of the learned-preconditioner family: harmonic star (eps <= 0.15), k ~ U[5, 25],
+    Np = 16, Mth = 96 (N = 24,576)."""
+    rs = wl.Stream(seed, 40 + i)
+    eps = 0.15 * rs.uniform()
+    k = 5.0 + 20.0 * rs.uniform()
+    d = wl.Stream(seed, 60 + i).directions(1)[0].tolist()
+    return wl.harmonic_star(seed, 200 + i, eps), k, d
+
+
+def run_learned(bie, n_train=4, n_test=2, steps=600):
+    """Learned preconditioner: train on systems of the family, then time FGMRES to 1e-8 on held-out
+    systems with the block-diagonal preconditioner (the judge and fallback) and with the network on
+    top of it.  Operator: the single layer S (first kind, weighted density), plane-wave data."""
+    import torch
+    ctx = bie.Context()
+    ggq = wl.load_ggq()
+    Np, Mt = 16, 96
+    block = 16 * Mt
+
+    def system(i):
+        desc, k, d = learned_family(1, i)
+        s = bie.Surface(ctx, desc, Np, Mt, ggq)
+        A = bie.assemble(s, bie.OP_S, k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = bie.BlockDiag(ctx, A, block)
+        t_lu = time.perf_counter() - t0
+        return s, A, B, k, d, t_lu
+
+    sets, lu_times = [], []
+    for i in range(n_train):
+        s, A, B, k, _, t_lu = system(i)
+        sets.append((bie.TrainSet(ctx, s, k, A, B), s, B))
+        lu_times.append(t_lu)
+        del A
+        torch.cuda.empty_cache()
+    net = bie.Net(ctx, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = net.train([t for t, _, _ in sets], steps=steps, batch=16, lr=1e-3, seed=2)
+    t_train = time.perf_counter() - t0
+    del sets
+    torch.cuda.empty_cache()
+    held = []
+    for j in range(n_test):
+        s, A, B, k, d, t_lu = system(1000 + j)
+        lu_times.append(t_lu)
+        g = bie.rhs(s, 0, d, k)
+        row = {"k": k}
+        for name, pc, prec in (("plain_fp64", bie.PRECOND_NONE, 0), ("block_fp64", bie.PRECOND_BLOCK, 0),
+                               ("block_mixed", bie.PRECOND_BLOCK, 1), ("learned_fp64", bie.PRECOND_LEARNED, 0)):
+            torch.cuda.synchronize()
+            try:
+                _, rep = bie.solve(ctx, A, g, tol=1e-8, restart=300, maxit=1500, prec=prec, precond=pc, block=B,
+                                   net=net, surface=s, k=k, raise_on_noconv=False)
+                row[name] = {kk: rep[kk] for kk in ("iterations", "refinements", "rel_residual", "seconds",
+                                                    "fallback_used")}
+                row[name]["converged"] = rep["status"] == 0
+            except bie.BieError as exc:
+                row[name] = {"error": str(exc)}
+        held.append(row)
+        del A, B
+        torch.cuda.empty_cache()
+    return {"operator": "S (first kind, weighted density), plane wave",
+            "family": "harmonic stars eps<=0.15, k~U[5,25], Np=16, Mth=96 (N=24,576)",
+            "train_systems": n_train, "train_steps": steps, "batch": 16, "train_seconds": t_train,
+            "loss_first10": float(np.mean(hist[:10])), "loss_last50": float(np.mean(hist[-50:])),
+            "blockdiag_factor_seconds": float(np.median(lu_times)), "held_out": held}
+
+
 def run_kernel_only(n):
     """One launch of the pair pipeline on n pairs (all sources of consecutive target rows)."""
     import torch
@@ -390,6 +461,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-preconditioner training and held-out solves")
     ap.add_argument("--batch-surfaces", type=int, default=8, help="surfaces in the batch-scheduler run (0: skip)")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: run the pair pipeline once on this many pairs of the workload and exit")

@@ -201,7 +201,7 @@ def assemble_near(surface, kernels, k, A, ws=1.0, wk=0.0):
 
 
 def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,
-          surface=None, k=0.0):
+          surface=None, k=0.0, raise_on_noconv=True):
     """FGMRES solve of A x = b (b: [N] or [nrhs, N]); returns (x, report dict).
 
     precond: 0 none, 1 block-diagonal (block), 2 learned (net on the grid of surface, wavenumber k,
@@ -217,7 +217,8 @@ def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=
     st = lib.bie_solve(ctx.h, n, _ptr(A), _ptr(bb), nrhs, _ptr(x), ctypes.byref(o), ctypes.byref(r))
     rep = {"iterations": r.iterations, "refinements": r.refinements, "rel_residual": r.rel_residual,
            "seconds": r.seconds, "fallback_used": r.fallback_used, "status": st}
-    check(st, "bie_solve")
+    if st != 4 or raise_on_noconv:   # 4 = BIE_ENOCONV: the report still holds the iterations and residual
+        check(st, "bie_solve")
     return x.reshape(b.shape), rep
 
 

@@ -334,6 +334,7 @@ struct bie_surface_s {
   double* near_coef;   // [dev] [3][16][16][16] = w_g L_n(x_g) on the reference panel
   double* ggq_x;       // [dev] [3][16][16]
   bie::cplx* tw;       // [dev] twiddles for length 12 Mt
+  float4* twf;         // [dev] the same twiddles as double words (re.h, re.l, im.h, im.l)
   double* thgrid;      // [dev] [Mt][3]: th_q = 2 pi q / Mt, sin(th_q/2), cos(th_q/2)
   int tw_len;
   double* host_t_nodes;

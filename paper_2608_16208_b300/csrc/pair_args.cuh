@@ -18,10 +18,11 @@ struct PairArgs {
   const double* ring_r;
   const double* ring_n;
   const cplx* tw;
+  const float4* twf;              // twiddles as double words
   const double* thg;              // [Mt][3]: th_q, sin(th_q/2), cos(th_q/2)
   const double* rec;              // recurrence coefficient table, 4 doubles per m (see pair_modes.cu)
   int rec_len;
-  double* scratch;                // per resident warp: (L + 1) x 32 doubles (A), + (L + 1) x 32 (D) if K
+  double* scratch;                // per resident warp: pair_scratch_per_warp(L, K) doubles
   int64_t scratch_per_warp;       // doubles
   const int64_t* rows;
   const int32_t* srcs;
@@ -32,6 +33,12 @@ struct PairArgs {
   int64_t w_ld;                   // complex elements between consecutive weight rows (Mt by default)
   int* status;
 };
+
+// Per-warp scratch (doubles): A_m (and D_m with the double layer) as [m][lane]; with the single
+// layer alone the D_m slot holds the phase table e^{i l a}, l = 0..32, as [pair][33] double words.
+__host__ __device__ inline int64_t pair_scratch_per_warp(int L, bool withK) {
+  return withK ? (int64_t)2 * (L + 1) * 32 : (int64_t)(L + 1) * 32 + 2 * 33 * 32;
+}
 
 PairArgs make_pair_args(bie_surface s, double k, unsigned kernels);
 bie_status launch_pairs(bie_surface s, PairArgs& a);

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "bie_internal.cuh"
+#include "dw.cuh"
 #include "pair_args.cuh"
 
 namespace bie {
@@ -138,6 +139,7 @@ struct PairInfo {
   int64_t row, ring;
   double t, th, ts, x, y, z;
   double a, b, a0;
+  double qb, om, sha, cha;   // e^{-b}, 1 - e^{-b}, sin(a/2), cos(a/2) (set with the root)
   int valid, bi, capped, pad;
 };
 
@@ -155,6 +157,10 @@ __device__ __forceinline__ PairInfo bcast(const PairInfo& p, int src) {
   o.a = __shfl_sync(0xffffffffu, p.a, src);
   o.b = __shfl_sync(0xffffffffu, p.b, src);
   o.a0 = __shfl_sync(0xffffffffu, p.a0, src);
+  o.qb = __shfl_sync(0xffffffffu, p.qb, src);
+  o.om = __shfl_sync(0xffffffffu, p.om, src);
+  o.sha = __shfl_sync(0xffffffffu, p.sha, src);
+  o.cha = __shfl_sync(0xffffffffu, p.cha, src);
   o.valid = __shfl_sync(0xffffffffu, p.valid, src);
   o.bi = __shfl_sync(0xffffffffu, p.bi, src);
   o.capped = __shfl_sync(0xffffffffu, p.capped, src);
@@ -231,8 +237,9 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
 // ------------------------------------------------------------------ phase C: A_m, D_m (one lane)
 // rec[4m..4m+3] = (2m-1)/(2m+1), 8m/(2m+1), 4m/(2m-1), (2m+1)/(2m-1)
 __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restrict__ rec, int rec_len, double* A,
-                                    double* D, int stride) {
-  // D may be null (only A is needed for the single-layer kernel)
+                                    double* D, int stride, bool dw_out) {
+  // D may be null (only A is needed for the single-layer kernel); dw_out: A is left as double words
+  // (float2 in the same 8-byte slots) for the double-word phase D
   const double q = exp(-b);
   double K, E;
   ellipke(q * q, -expm1(-2 * b), &K, &E);
@@ -251,6 +258,8 @@ __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restr
       A[(m + 1) * stride] = am;
       if (D) D[(m + 1) * stride] = dm;
     }
+    if (dw_out)
+      for (int m = 0; m <= L; ++m) reinterpret_cast<float2*>(A)[m * stride] = dw_from(A[m * stride]);
     return;
   }
   // Miller: backward from N with A~_{N+1} = 0, A~_N = 1; rescale on growth; normalise by A_0.
@@ -278,6 +287,8 @@ __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restr
     prevA = am;
   }
   if (D) D[0] = A[0] - A[stride];
+  if (dw_out)
+    for (int m = 0; m <= L; ++m) reinterpret_cast<float2*>(A)[m * stride] = dw_from(A[m * stride]);
 }
 
 // ------------------------------------------------------------------ small helpers of phase D
@@ -355,6 +366,178 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
   }
   __syncwarp();
   return warp_fft(X, Y, P, tw, T, +1);
+}
+
+// ------------------------------------------------------------------ phase D, single layer alone
+// The same steps as the general phase D below, with every transform, the upsampling, the products
+// and the unpacking in double-word arithmetic (dw.cuh); FP64 for the samples and the outputs.
+//   E       [pair][33] double-word e^{i l a} (l < 32) and e^{32 i a} of the batch (phase B)
+//   scrA    A_m as double words, [m][lane]
+__device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const double* scrA, const float4* E,
+                                               const PairInfo& mine, unsigned valid_mask, int64_t p0, int nb) {
+  const int lane = threadIdx.x & 31;
+  const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
+  float4* W0 = reinterpret_cast<float4*>(sm.W0);
+  float4* W1 = reinterpret_cast<float4*>(sm.W1);
+  float2* Acal = reinterpret_cast<float2*>(sm.Acal);
+  float4* ph = reinterpret_cast<float4*>(sm.ph);   // e^{ija} / Mt, j = -M..M
+  float4* kc = reinterpret_cast<float4*>(sm.kc);
+  const float2* Ad = reinterpret_cast<const float2*>(scrA);
+  const float2 invMt = dw_from(1.0 / Mt);
+  const float2 ratio = dw_from((double)Mt / P);   // e^{ija}/Mt -> e^{ija}/P
+  int acal_next = -1;   // pair whose circulant transform already sits in Acal
+  for (int pi = 0; pi < nb; ++pi) {
+    const PairInfo pr = bcast(mine, pi);
+    const int64_t p = a.out_mod ? (a.out_base + p0 + pi) % a.out_mod : p0 + pi;   // output slot
+    if (!pr.valid) {
+      if (a.modes_out)
+        for (int m = lane; m < 2 * (Mt + 1); m += 32) a.modes_out[p * 2 * (Mt + 1) + m] = 0.0;
+      if (a.weights_out)
+        for (int m = lane; m < Mt; m += 32) a.weights_out[p * a.w_ld + m] = C(0.0);
+      continue;
+    }
+    const double* rr = a.ring_r + pr.ring * 3 * Mt;
+    const double dts = fabs(pr.t - pr.ts);
+    // ---- phases e^{ija}/Mt: lane l starts from e^{i l a}, steps of e^{32 i a}
+    {
+      float4 e = E[pi * 33 + lane];
+      const float4 step = E[pi * 33 + 32];
+      for (int j = lane; j <= M; j += 32) {
+        const float4 es = dwc_mulr(e, invMt);
+        ph[M + j] = es;
+        ph[M - j] = dwc_conj(es);
+        e = dwc_mul(e, step);
+      }
+    }
+    // ---- circulant transform of A_{|d|}, unless it came packed with the previous pair
+    if (acal_next != pi) {
+      for (int pp = lane; pp < P; pp += 32) {
+        const int dd = pp <= P / 2 ? pp : P - pp;
+        W1[pp] = mkc(dd <= L ? Ad[dd * 32 + pi] : make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+      }
+      __syncwarp();
+      const float4* Af = warp_fft_dw(W1, W0, P, a.twf, a.T, -1);
+      for (int pp = lane; pp < P; pp += 32) Acal[pp] = cre(Af[pp]);
+    }
+    __syncwarp();
+    // ---- samples: F + i cos(k rho) (double words), sin(k rho)/rho (FP64)
+    for (int q = lane; q < Mt; q += 32) {
+      const double thq = a.thg[3 * q];
+      const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta;
+      double yx, yy, yz;
+      if (near) {
+        const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
+        yx = Y.x; yy = Y.y; yz = Y.z;
+      } else {
+        yx = rr[3 * q] - pr.x; yy = rr[3 * q + 1] - pr.y; yz = rr[3 * q + 2] - pr.z;
+      }
+      const double r2 = yx * yx + yy * yy + yz * yz;
+      const double rinv = rsqrt(r2);
+      const double rho = r2 * rinv;
+      const double dq = thq - pr.a;
+      const double sp = fabs(dq) < 0.1 ? sin(0.5 * dq) : a.thg[3 * q + 1] * pr.cha - a.thg[3 * q + 2] * pr.sha;
+      const double sv = pr.om * pr.om + 4 * pr.qb * sp * sp;
+      const double F = sqrt(sv) * rinv;
+      double skr, ckr;
+      sincos(a.k * rho, &skr, &ckr);
+      W0[q] = mkc(dw_from(F), dw_from(ckr));
+      sm.sn[q] = skr * rinv;
+    }
+    __syncwarp();
+    // ---- modes of F and cos(k rho); upsample onto the shifted P grid
+    float4* Z1 = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
+    float4* X = (Z1 == W0) ? W1 : W0;
+    for (int pp = lane; pp < P; pp += 32) X[pp] = dwc_zero();
+    __syncwarp();
+    for (int jj = lane; jj <= 2 * M; jj += 32) {
+      const int jv = jj - M;
+      float4 z = dwc_mul(ph[jj], Z1[wrapi(jv, Mt)]);
+      if (jv == M || jv == -M) z = dwc_scale2(z, 0.5f);
+      X[wrapi(jv, P)] = z;
+    }
+    __syncwarp();
+    float4* up1 = warp_fft_dw(X, Z1, P, a.twf, a.T, +1);   // re: F~, im: C~
+    float4* uf = (up1 == W0) ? W1 : W0;
+    // ---- U = F~ C~ Acal in the real part, the next valid pair's circulant in the imaginary part.
+    // Each part comes out of the shared transform with an error in proportion to the other's size
+    // (the product is 10^3 times the circulant next to a pole), so the circulant is scaled by an
+    // exact power of two to the product's root-mean-square size before packing.
+    const unsigned later = valid_mask & ~((2u << pi) - 1u);
+    const int nxt = later ? __ffs(later) - 1 : nb;
+    const bool pack = nxt < nb;
+    float su = 0.f, sa = 0.f;
+    for (int pp = lane; pp < P; pp += 32) {
+      const int dd = pp <= P / 2 ? pp : P - pp;
+      const float4 u = up1[pp];
+      const float2 prod = dw_mul(dw_mul(cre(u), cim(u)), Acal[pp]);
+      const float2 an = (pack && dd <= L) ? Ad[dd * 32 + nxt] : make_float2(0.f, 0.f);
+      su = fmaf(prod.x, prod.x, su);
+      sa = fmaf(an.x, an.x, sa);
+      uf[pp] = mkc(prod, an);
+    }
+    for (int o = 16; o; o >>= 1) {
+      su += __shfl_xor_sync(0xffffffffu, su, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    int pe = 0;   // circulant scale 2^pe
+    if (pack && sa > 0.f && su > 0.f) pe = max(-60, min(60, (int)rintf(0.5f * log2f(su / sa))));
+    if (pe) {
+      const float sc = ldexpf(1.f, pe);
+      __syncwarp();
+      for (int pp = lane; pp < P; pp += 32) {
+        uf[pp].z *= sc;
+        uf[pp].w *= sc;
+      }
+    }
+    __syncwarp();
+    const float4* Yf = warp_fft_dw(uf, up1, P, a.twf, a.T, -1);
+    // ---- kernel modes kc_m = e^{-ima} Re-part transform / P; the packed circulant transform
+    for (int jj = lane; jj <= 2 * M; jj += 32) {
+      const int m = jj - M;
+      const float4 zp = Yf[wrapi(m, P)], zm = dwc_conj(Yf[wrapi(-m, P)]);
+      kc[jj] = dwc_mul(dwc_mulr(dwc_conj(ph[jj]), ratio), dwc_scale2(dwc_add(zp, zm), 0.5f));
+    }
+    if (pack) {
+      const float unsc = ldexpf(0.5f, -pe);
+      for (int pp = lane; pp < P; pp += 32) {
+        const float4 zp = Yf[pp], zm = dwc_conj(Yf[(P - pp) % P]);
+        Acal[pp] = dw_scale2(dw_sub(cim(zp), cim(zm)), unsc);
+      }
+      acal_next = nxt;
+    }
+    __syncwarp();
+    // ---- outputs: modes K_m = kc_m + i <sin(k rho)/rho>_m, and / or the Parseval weights
+    if (a.modes_out) {
+      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(dw_from(sm.sn[q]), make_float2(0.f, 0.f));
+      __syncwarp();
+      const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
+      double* out = a.modes_out + p * 2 * (Mt + 1);
+      for (int mm = lane; mm <= 2 * M; mm += 32) {
+        const int m = mm - M;
+        cplx sv = dwc_to(Sf[wrapi(m, Mt)]) * (1.0 / Mt);
+        if (m == M || m == -M) sv = 0.5 * sv;
+        const cplx sg = dwc_to(kc[mm]);
+        out[2 * mm] = sg.re - sv.im;
+        out[2 * mm + 1] = sg.im + sv.re;
+      }
+      __syncwarp();
+    }
+    if (a.weights_out) {
+      for (int q = lane; q < Mt; q += 32) {
+        const int m = q < M ? q : q - Mt;
+        W0[q] = (q == M) ? dwc_scale2(dwc_add(kc[2 * M], kc[0]), 0.5f) : kc[m + M];
+      }
+      __syncwarp();
+      const float4* Wt = warp_fft_dw(W0, W1, Mt, a.twf, a.T, +1);
+      cplx* wout = a.weights_out + p * a.w_ld;
+      for (int q = lane; q < Mt; q += 32) {
+        const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
+        wout[q] = C(w.re, w.im + sm.sn[q] / Mt);
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -444,10 +627,27 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
     // ---------------- B. complex root and C. A_m, D_m (lane per pair)
     if (lane < nb && mine.valid) {
       locate_root(a.S, Mt, mine);
-      const PairInfo& pr = mine;
-      a_modes_lane(pr.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32);
+      mine.qb = exp(-mine.b);
+      mine.om = -expm1(-mine.b);
+      sincos(0.5 * mine.a, &mine.sha, &mine.cha);
+      if (!wantK) {
+        // e^{i l a} for l = 0..31 by rotation and e^{32 i a} directly, as double words ([pair][33])
+        float4* E = reinterpret_cast<float4*>(scrD) + lane * 33;
+        const cplx e1 = C(mine.cha * mine.cha - mine.sha * mine.sha, 2 * mine.sha * mine.cha);
+        cplx e = C(1.0);
+        for (int l = 0; l < 32; ++l) {
+          E[l] = dwc_from(e);
+          e = e * e1;
+        }
+        E[32] = dwc_from(cexpi(32.0 * mine.a));
+      }
+      a_modes_lane(mine.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32, !wantK);
     }
     __syncwarp();
+    if constexpr (!kWithK) {
+      phase_d_single(a, sm, scrA, reinterpret_cast<const float4*>(scrD), mine, valid_mask, p0, nb);
+      return;
+    }
     // ---------------- D. per pair (warp)
     int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
@@ -887,6 +1087,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.ring_r = s->ring_r;
   a.ring_n = s->ring_n;
   a.tw = s->tw;
+  a.twf = s->twf;
   a.thg = s->thgrid;
   a.w_ld = s->Mt;
   a.status = s->ctx->d_status;
@@ -946,7 +1147,7 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
     const bie_status rs = ensure_rec(s->ctx->stream, a.L);
     if (rs != BIE_OK) return rs;
   }
-  a.scratch_per_warp = (int64_t)(withK ? 2 : 1) * (a.L + 1) * 32;
+  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK);
   const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
   if (g_res.scratch_bytes < sbytes) {
     cudaStreamSynchronize(s->ctx->stream);
@@ -1069,7 +1270,7 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
   a.rec = st.rec;
   a.rec_len = kNoAllocRecLen;
   a.scratch = st.scratch;
-  a.scratch_per_warp = (int64_t)(withK ? 2 : 1) * (a.L + 1) * 32;   // <= 2 (kNoAllocMaxL + 1) 32
+  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK);   // <= 2 (kNoAllocMaxL + 1) 32
   kern<<<kNoAllocBlocks, 32 * wpb, smem, ctx->stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch (no-alloc)");
@@ -1233,7 +1434,7 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch)"); }
   e = cudaMemcpy(b->d_args, b->host_args.data(), sizeof(PairArgs) * n_surf, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "cudaMemcpy(batch args)"); }
-  b->scratch_per_warp = (int64_t)(b->withK ? 2 : 1) * ((b->withK ? 4 : 3) * (b->maxMt / 2) + 1) * 32;
+  b->scratch_per_warp = pair_scratch_per_warp((b->withK ? 4 : 3) * (b->maxMt / 2), b->withK);
   // ---- autotuner: item size x CTA shape, timed on a prefix of the work list (about 1/16 of the pairs)
   const int item_cands[3] = {256, 1024, 4096};
   const int wpb_cands[3] = {1, 2, 4};

@@ -145,9 +145,13 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   // twiddles for length 12 Mt
   const int T = 12 * Mt;
   std::vector<cplx> tw(T);
+  std::vector<float4> twf(T);   // the same table as double words (h + l, rounded from long double)
   for (int k = 0; k < T; ++k) {
     long double a = -2.0L * 3.14159265358979323846264338327950288L * k / T;
-    tw[k] = C((double)cosl(a), (double)sinl(a));
+    const long double c = cosl(a), sn = sinl(a);
+    tw[k] = C((double)c, (double)sn);
+    const float ch = (float)c, sh = (float)sn;
+    twf[k] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
   }
   s->tw_len = T;
   std::vector<double> thg(3 * Mt);
@@ -174,6 +178,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   ALLOC(s->near_coef, sizeof(double) * coef.size());
   ALLOC(s->ggq_x, sizeof(double) * 3 * 16 * 16);
   ALLOC(s->tw, sizeof(cplx) * T);
+  ALLOC(s->twf, sizeof(float4) * T);
   ALLOC(s->thgrid, sizeof(double) * 3 * Mt);
 #undef ALLOC
   cudaStream_t st = ctx->stream;
@@ -185,6 +190,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   H2D(s->near_coef, coef.data(), sizeof(double) * coef.size());
   H2D(s->ggq_x, &ggq->x[0][0][0], sizeof(double) * 3 * 16 * 16);
   H2D(s->tw, tw.data(), sizeof(cplx) * T);
+  H2D(s->twf, twf.data(), sizeof(float4) * T);
   H2D(s->thgrid, thg.data(), sizeof(double) * 3 * Mt);
 #undef H2D
   const int threads = 256;
@@ -204,7 +210,7 @@ void bie_surface_free(bie_surface s) {
   if (!s) return;
   cudaFree(s->t_nodes); cudaFree(s->pts); cudaFree(s->nrm); cudaFree(s->jac);
   cudaFree(s->ring_t); cudaFree(s->ring_r); cudaFree(s->ring_n);
-  cudaFree(s->near_coef); cudaFree(s->ggq_x); cudaFree(s->tw); cudaFree(s->thgrid);
+  cudaFree(s->near_coef); cudaFree(s->ggq_x); cudaFree(s->tw); cudaFree(s->twf); cudaFree(s->thgrid);
   delete[] s->host_t_nodes;
   delete s;
 }
