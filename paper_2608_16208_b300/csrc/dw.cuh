@@ -48,11 +48,34 @@ __device__ __forceinline__ float2 dw_mul(float2 x, float2 y) {
 __device__ __forceinline__ float2 dw_scale2(float2 x, float s) {   // s a power of two: exact
   return make_float2(x.x * s, x.y * s);
 }
+// double -> double word by splitting the significand with integer operations (the FP32 <-> FP64
+// conversion instructions run on the narrow FP64 pipe): h = the top 24 significand bits (truncated),
+// l = the remaining 29 bits rounded to a float, same sign.  Outside 2^-126 .. 2^115 plain conversions.
 __device__ __forceinline__ float2 dw_from(double v) {
-  const float h = __double2float_rn(v);
-  return make_float2(h, __double2float_rn(v - (double)h));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 897 || e > 1138) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const float rest = __uint2float_rn((unsigned)(b & 0x1fffffffu));
+  const float l = (__uint_as_float(sgn | __float_as_uint(rest)) * 5.421010862427522e-20f)   // * 2^-64
+                  * __uint_as_float((unsigned)(e - 884) << 23);                            // * 2^(e - 1011)
+  return make_float2(h, l);
 }
-__device__ __forceinline__ double dw_to(float2 a) { return (double)a.x + (double)a.y; }
+// float -> double exactly from the bit pattern (zero and subnormal floats give a signed zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0xffu) return (double)f;
+  const unsigned long long sg = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ef == 0) return __longlong_as_double((long long)sg);
+  return __longlong_as_double((long long)(sg | ((unsigned long long)(ef + 896) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double dw_to(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
 
 // complex helpers on float4 = (re.h, re.l, im.h, im.l)
 __device__ __forceinline__ float2 cre(float4 a) { return make_float2(a.x, a.y); }
@@ -96,6 +119,43 @@ __device__ __forceinline__ float4 dwc_mul(float4 x, float4 y) {
 }
 // complex times real double-word
 __device__ __forceinline__ float4 dwc_mulr(float4 x, float2 r) { return mkc(dw_mul(cre(x), r), dw_mul(cim(x), r)); }
+
+// ------------------------------------------------------------------ sin and cos
+// sin x, cos x for |x| < 1e4 (FP64 argument): Cody-Waite reduction by pi/2 in FP64 (two-part constant
+// with FMA: r = x - n pi/2 to about 1e-16 absolute), then the Taylor series of sin r / r and cos r in
+// r^2 for |r| <= pi/4: the terms r^10 .. r^16 (below 2.3e-9) in FP32, the leading five in double
+// words.  Absolute error about 1e-14.
+__device__ __forceinline__ void dw_sincos(double x, float2* sn, float2* cs) {
+  const double n = rint(x * 0.63661977236758138);
+  double r = fma(-n, 1.5707963267948966, x);
+  r = fma(-n, 6.123233995736766e-17, r);
+  const float2 rw = dw_from(r);
+  const float2 r2 = dw_mul(rw, rw);
+  const float xf = r2.x;
+  // (-1)^k / (2k+1)! and (-1)^k / (2k)!, k = 5..8 (FP32) and k = 0..4 (double words)
+  float ts = fmaf(fmaf(fmaf(2.8114573589663704e-15f, xf, -7.647163609812713e-13f), xf, 1.6059044372074283e-10f), xf,
+                  -2.5052107943679403e-08f);
+  float tc = fmaf(fmaf(fmaf(4.7794772561329454e-14f, xf, -1.147074536050896e-11f), xf, 2.0876755879584152e-09f), xf,
+                  -2.755731998149713e-07f);
+  float2 ps = make_float2(ts, 0.f), pc = make_float2(tc, 0.f);
+  ps = dw_add(dw_mul(ps, r2), make_float2(2.7557318844628753e-06f, 3.793571224297229e-14f));
+  pc = dw_add(dw_mul(pc, r2), make_float2(2.4801587642286904e-05f, -3.40699609366682e-13f));
+  ps = dw_add(dw_mul(ps, r2), make_float2(-0.00019841270113829523f, 2.725596874933456e-12f));
+  pc = dw_add(dw_mul(pc, r2), make_float2(-0.0013888889225199819f, 3.3631094437103215e-11f));
+  ps = dw_add(dw_mul(ps, r2), make_float2(0.008333333767950535f, -4.34617203337595e-10f));
+  pc = dw_add(dw_mul(pc, r2), make_float2(0.0416666679084301f, -1.2417634698280722e-09f));
+  ps = dw_add(dw_mul(ps, r2), make_float2(-0.1666666716337204f, 4.967053879312289e-09f));
+  pc = dw_add(dw_mul(pc, r2), make_float2(-0.5f, 0.f));
+  ps = dw_add(dw_mul(ps, r2), make_float2(1.f, 0.f));
+  pc = dw_add(dw_mul(pc, r2), make_float2(1.f, 0.f));
+  const float2 sr = dw_mul(ps, rw);
+  switch ((int)n & 3) {
+    case 0: *sn = sr; *cs = pc; break;
+    case 1: *sn = pc; *cs = dw_neg(sr); break;
+    case 2: *sn = dw_neg(sr); *cs = dw_neg(pc); break;
+    default: *sn = dw_neg(pc); *cs = sr; break;
+  }
+}
 
 // ------------------------------------------------------------------ warp FFT
 // Same transform and buffer contract as warp_fft (Stockham, radices 4, 2, 3; the result lands in

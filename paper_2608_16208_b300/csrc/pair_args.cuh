@@ -35,9 +35,10 @@ struct PairArgs {
 };
 
 // Per-warp scratch (doubles): A_m (and D_m with the double layer) as [m][lane]; with the single
-// layer alone the D_m slot holds the phase table e^{i l a}, l = 0..32, as [pair][33] double words.
-__host__ __device__ inline int64_t pair_scratch_per_warp(int L, bool withK) {
-  return withK ? (int64_t)2 * (L + 1) * 32 : (int64_t)(L + 1) * 32 + 2 * 33 * 32;
+// layer alone the D_m slot holds the phase table e^{i l a}, l = 0..32, as [pair][33] double words,
+// followed by rho^2 on the ring of every pair of the batch, [pair][Mt].
+__host__ __device__ inline int64_t pair_scratch_per_warp(int L, bool withK, int Mt) {
+  return withK ? (int64_t)2 * (L + 1) * 32 : (int64_t)(L + 1) * 32 + 2 * 33 * 32 + (int64_t)32 * Mt;
 }
 
 PairArgs make_pair_args(bie_surface s, double k, unsigned kernels);

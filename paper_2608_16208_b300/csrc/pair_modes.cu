@@ -373,8 +373,10 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
 // and the unpacking in double-word arithmetic (dw.cuh); FP64 for the samples and the outputs.
 //   E       [pair][33] double-word e^{i l a} (l < 32) and e^{32 i a} of the batch (phase B)
 //   scrA    A_m as double words, [m][lane]
+//   R2      rho^2 on the ring, [pair][Mt] (phase A, with the cancellation-free differences)
 __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const double* scrA, const float4* E,
-                                               const PairInfo& mine, unsigned valid_mask, int64_t p0, int nb) {
+                                               const double* R2, const PairInfo& mine, unsigned valid_mask,
+                                               int64_t p0, int nb) {
   const int lane = threadIdx.x & 31;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
   float4* W0 = reinterpret_cast<float4*>(sm.W0);
@@ -396,8 +398,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
         for (int m = lane; m < Mt; m += 32) a.weights_out[p * a.w_ld + m] = C(0.0);
       continue;
     }
-    const double* rr = a.ring_r + pr.ring * 3 * Mt;
-    const double dts = fabs(pr.t - pr.ts);
+    const double* r2p = R2 + pi * Mt;
     // ---- phases e^{ija}/Mt: lane l starts from e^{i l a}, steps of e^{32 i a}
     {
       float4 e = E[pi * 33 + lane];
@@ -420,28 +421,21 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       for (int pp = lane; pp < P; pp += 32) Acal[pp] = cre(Af[pp]);
     }
     __syncwarp();
-    // ---- samples: F + i cos(k rho) (double words), sin(k rho)/rho (FP64)
+    // ---- samples: F + i cos(k rho) and sin(k rho)/rho, as double words
+    float2* snw = reinterpret_cast<float2*>(sm.sn);
     for (int q = lane; q < Mt; q += 32) {
       const double thq = a.thg[3 * q];
-      const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta;
-      double yx, yy, yz;
-      if (near) {
-        const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
-        yx = Y.x; yy = Y.y; yz = Y.z;
-      } else {
-        yx = rr[3 * q] - pr.x; yy = rr[3 * q + 1] - pr.y; yz = rr[3 * q + 2] - pr.z;
-      }
-      const double r2 = yx * yx + yy * yy + yz * yz;
+      const double r2 = r2p[q];
       const double rinv = rsqrt(r2);
       const double rho = r2 * rinv;
       const double dq = thq - pr.a;
       const double sp = fabs(dq) < 0.1 ? sin(0.5 * dq) : a.thg[3 * q + 1] * pr.cha - a.thg[3 * q + 2] * pr.sha;
       const double sv = pr.om * pr.om + 4 * pr.qb * sp * sp;
       const double F = sqrt(sv) * rinv;
-      double skr, ckr;
-      sincos(a.k * rho, &skr, &ckr);
-      W0[q] = mkc(dw_from(F), dw_from(ckr));
-      sm.sn[q] = skr * rinv;
+      float2 skr, ckr;
+      dw_sincos(a.k * rho, &skr, &ckr);
+      W0[q] = mkc(dw_from(F), ckr);
+      snw[q] = dw_mul(skr, dw_from(rinv));
     }
     __syncwarp();
     // ---- modes of F and cos(k rho); upsample onto the shifted P grid
@@ -508,7 +502,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     __syncwarp();
     // ---- outputs: modes K_m = kc_m + i <sin(k rho)/rho>_m, and / or the Parseval weights
     if (a.modes_out) {
-      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(dw_from(sm.sn[q]), make_float2(0.f, 0.f));
+      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(snw[q], make_float2(0.f, 0.f));
       __syncwarp();
       const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
       double* out = a.modes_out + p * 2 * (Mt + 1);
@@ -532,7 +526,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       cplx* wout = a.weights_out + p * a.w_ld;
       for (int q = lane; q < Mt; q += 32) {
         const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
-        wout[q] = C(w.re, w.im + sm.sn[q] / Mt);
+        wout[q] = C(w.re, w.im + dw_to(snw[q]) * (1.0 / Mt));
       }
       __syncwarp();
     }
@@ -590,11 +584,12 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       mine = pr;
     }
     const unsigned valid_mask = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
-    // ---------------- A. grid minimiser (warp per pair)
-    double* rho2 = (double*)sm.W0;   // FFT buffer reused as Mt-length scratch in this pass
+    // ---------------- A. grid minimiser (warp per pair); rho^2 kept in scratch for the single layer
+    double* R2 = wantK ? nullptr : scrD + 2 * 33 * 32;
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = bcast(mine, pi);
       if (!pr.valid) continue;
+      double* rho2 = wantK ? (double*)sm.W0 : R2 + pi * Mt;
       const double* rr = a.ring_r + pr.ring * 3 * Mt;
       const int i = (int)(pr.row % Mt);
       const double dts = fabs(pr.t - pr.ts);
@@ -641,11 +636,13 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         }
         E[32] = dwc_from(cexpi(32.0 * mine.a));
       }
+      // FP64 recurrences (Miller runs up to L + 20/b steps: its rounding would add up in double words);
+      // the single layer keeps A_m as double words for its transforms
       a_modes_lane(mine.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32, !wantK);
     }
     __syncwarp();
     if constexpr (!kWithK) {
-      phase_d_single(a, sm, scrA, reinterpret_cast<const float4*>(scrD), mine, valid_mask, p0, nb);
+      phase_d_single(a, sm, scrA, reinterpret_cast<const float4*>(scrD), R2, mine, valid_mask, p0, nb);
       return;
     }
     // ---------------- D. per pair (warp)
@@ -1147,7 +1144,7 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
     const bie_status rs = ensure_rec(s->ctx->stream, a.L);
     if (rs != BIE_OK) return rs;
   }
-  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK);
+  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK, a.Mt);
   const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
   if (g_res.scratch_bytes < sbytes) {
     cudaStreamSynchronize(s->ctx->stream);
@@ -1270,7 +1267,7 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
   a.rec = st.rec;
   a.rec_len = kNoAllocRecLen;
   a.scratch = st.scratch;
-  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK);   // <= 2 (kNoAllocMaxL + 1) 32
+  a.scratch_per_warp = pair_scratch_per_warp(a.L, withK, a.Mt);   // <= 2 (kNoAllocMaxL + 1) 32
   kern<<<kNoAllocBlocks, 32 * wpb, smem, ctx->stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch (no-alloc)");
@@ -1434,7 +1431,7 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch)"); }
   e = cudaMemcpy(b->d_args, b->host_args.data(), sizeof(PairArgs) * n_surf, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "cudaMemcpy(batch args)"); }
-  b->scratch_per_warp = pair_scratch_per_warp((b->withK ? 4 : 3) * (b->maxMt / 2), b->withK);
+  b->scratch_per_warp = pair_scratch_per_warp((b->withK ? 4 : 3) * (b->maxMt / 2), b->withK, b->maxMt);
   // ---- autotuner: item size x CTA shape, timed on a prefix of the work list (about 1/16 of the pairs)
   const int item_cands[3] = {256, 1024, 4096};
   const int wpb_cands[3] = {1, 2, 4};
