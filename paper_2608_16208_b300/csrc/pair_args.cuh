@@ -32,6 +32,11 @@ struct PairArgs {
   int64_t out_base, out_mod;      // output slot of pair p: (out_base + p) % out_mod when out_mod > 0
   int64_t w_ld;                   // complex elements between consecutive weight rows (Mt by default)
   int* status;
+  // single layer, split launch: one record per pair of the chunk, written by the root kernel
+  double* rec_hdr;                // [pair][8]: a, e^{-b}, 1 - e^{-b}, sin(a/2), cos(a/2), valid
+  float4* rec_E;                  // [pair][33]: e^{i l a}, l < 32, and e^{32 i a} as double words
+  double* rec_A;                  // [pair][L + 1]: A_m as double words
+  double* rec_R2;                 // [pair][Mt]: rho^2 on the ring
 };
 
 // Per-warp scratch (doubles): A_m (and D_m with the double layer) as [m][lane]; with the single

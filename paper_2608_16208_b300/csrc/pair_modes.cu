@@ -372,11 +372,11 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
 // The same steps as the general phase D below, with every transform, the upsampling, the products
 // and the unpacking in double-word arithmetic (dw.cuh); FP64 for the samples and the outputs.
 //   E       [pair][33] double-word e^{i l a} (l < 32) and e^{32 i a} of the batch (phase B)
-//   scrA    A_m as double words, [m][lane]
+//   Ab      A_m as double words: A_m of pair j at Ab[j a_ps + m a_ms]
 //   R2      rho^2 on the ring, [pair][Mt] (phase A, with the cancellation-free differences)
-__device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const double* scrA, const float4* E,
-                                               const double* R2, const PairInfo& mine, unsigned valid_mask,
-                                               int64_t p0, int nb) {
+__device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const float2* Ab, int a_ps, int a_ms,
+                                               const float4* E, const double* R2, const PairInfo& mine,
+                                               unsigned valid_mask, int64_t p0, int nb) {
   const int lane = threadIdx.x & 31;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
   float4* W0 = reinterpret_cast<float4*>(sm.W0);
@@ -384,7 +384,6 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
   float2* Acal = reinterpret_cast<float2*>(sm.Acal);
   float4* ph = reinterpret_cast<float4*>(sm.ph);   // e^{ija} / Mt, j = -M..M
   float4* kc = reinterpret_cast<float4*>(sm.kc);
-  const float2* Ad = reinterpret_cast<const float2*>(scrA);
   const float2 invMt = dw_from(1.0 / Mt);
   const float2 ratio = dw_from((double)Mt / P);   // e^{ija}/Mt -> e^{ija}/P
   int acal_next = -1;   // pair whose circulant transform already sits in Acal
@@ -414,7 +413,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     if (acal_next != pi) {
       for (int pp = lane; pp < P; pp += 32) {
         const int dd = pp <= P / 2 ? pp : P - pp;
-        W1[pp] = mkc(dd <= L ? Ad[dd * 32 + pi] : make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+        W1[pp] = mkc(dd <= L ? Ab[pi * a_ps + dd * a_ms] : make_float2(0.f, 0.f), make_float2(0.f, 0.f));
       }
       __syncwarp();
       const float4* Af = warp_fft_dw(W1, W0, P, a.twf, a.T, -1);
@@ -464,7 +463,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       const int dd = pp <= P / 2 ? pp : P - pp;
       const float4 u = up1[pp];
       const float2 prod = dw_mul(dw_mul(cre(u), cim(u)), Acal[pp]);
-      const float2 an = (pack && dd <= L) ? Ad[dd * 32 + nxt] : make_float2(0.f, 0.f);
+      const float2 an = (pack && dd <= L) ? Ab[nxt * a_ps + dd * a_ms] : make_float2(0.f, 0.f);
       su = fmaf(prod.x, prod.x, su);
       sa = fmaf(an.x, an.x, sa);
       uf[pp] = mkc(prod, an);
@@ -535,17 +534,19 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
 }
 
 // ------------------------------------------------------------------ the kernel
-// One batch of up to 32 consecutive pairs [p0, p0 + nb) of the argument set a (phases A-D).
+// Decode and phases A-C of one batch of up to 32 consecutive pairs [p0, p0 + nb).  Outputs per
+// pair j of the batch: rho^2 on the ring at R2 + j Mt (single layer; shared memory with the double
+// layer); e^{i l a} at E + 33 j (single layer); A_m at Ab + j a_ps + m a_ms (double words for the
+// single layer); D_m at scrD + j + 32 m (double layer).
 template <bool kWithK>
-__device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm, double* scrA, double* scrD,
-                                              int64_t p0, int nb) {
+__device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, int64_t p0, int nb, double* R2,
+                                            float4* E, double* Ab, int a_ps, int a_ms, double* scrD, PairInfo& mine,
+                                            unsigned& valid_mask) {
   const int lane = threadIdx.x & 31;
-  const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
-  const bool wantS = a.kernels & BIE_KERNEL_S;
+  const int Mt = a.Mt, L = a.L;
   constexpr bool wantK = kWithK;
-  const int nk = (wantS ? 1 : 0) + (wantK ? 1 : 0);
     // ---------------- decode the batch (lane per pair)
-    PairInfo mine = {};
+    mine = PairInfo{};
     if (lane < nb) {
       const int64_t p = p0 + lane;
       int64_t row;
@@ -583,9 +584,8 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       }
       mine = pr;
     }
-    const unsigned valid_mask = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
-    // ---------------- A. grid minimiser (warp per pair); rho^2 kept in scratch for the single layer
-    double* R2 = wantK ? nullptr : scrD + 2 * 33 * 32;
+    valid_mask = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
+    // ---------------- A. grid minimiser (warp per pair); rho^2 kept for the single layer
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = bcast(mine, pi);
       if (!pr.valid) continue;
@@ -627,24 +627,38 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       sincos(0.5 * mine.a, &mine.sha, &mine.cha);
       if (!wantK) {
         // e^{i l a} for l = 0..31 by rotation and e^{32 i a} directly, as double words ([pair][33])
-        float4* E = reinterpret_cast<float4*>(scrD) + lane * 33;
+        float4* El = E + lane * 33;
         const cplx e1 = C(mine.cha * mine.cha - mine.sha * mine.sha, 2 * mine.sha * mine.cha);
         cplx e = C(1.0);
         for (int l = 0; l < 32; ++l) {
-          E[l] = dwc_from(e);
+          El[l] = dwc_from(e);
           e = e * e1;
         }
-        E[32] = dwc_from(cexpi(32.0 * mine.a));
+        El[32] = dwc_from(cexpi(32.0 * mine.a));
       }
       // FP64 recurrences (Miller runs up to L + 20/b steps: its rounding would add up in double words);
       // the single layer keeps A_m as double words for its transforms
-      a_modes_lane(mine.b, L, a.rec, a.rec_len, scrA + lane, wantK ? scrD + lane : nullptr, 32, !wantK);
+      a_modes_lane(mine.b, L, a.rec, a.rec_len, Ab + lane * a_ps, wantK ? scrD + lane : nullptr, a_ms, !wantK);
     }
     __syncwarp();
+}
+
+// One batch of up to 32 consecutive pairs [p0, p0 + nb) of the argument set a (phases A-D).
+template <bool kWithK>
+__device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm, double* scrA, double* scrD,
+                                              int64_t p0, int nb) {
+  const int lane = threadIdx.x & 31;
+  const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
+  const bool wantS = a.kernels & BIE_KERNEL_S;
+  constexpr bool wantK = kWithK;
+  const int nk = (wantS ? 1 : 0) + (wantK ? 1 : 0);
+    PairInfo mine;
+    unsigned valid_mask;
+    double* R2 = wantK ? nullptr : scrD + 2 * 33 * 32;
+    front_batch<kWithK>(a, sm, p0, nb, R2, reinterpret_cast<float4*>(scrD), scrA, 1, 32, scrD, mine, valid_mask);
     if constexpr (!kWithK) {
-      phase_d_single(a, sm, scrA, reinterpret_cast<const float4*>(scrD), R2, mine, valid_mask, p0, nb);
-      return;
-    }
+      phase_d_single(a, sm, reinterpret_cast<const float2*>(scrA), 1, 32, reinterpret_cast<const float4*>(scrD), R2, mine, valid_mask, p0, nb);
+    } else {
     // ---------------- D. per pair (warp)
     int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
@@ -1025,6 +1039,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         }
       }
     }
+    }
     __syncwarp();
 }
 
@@ -1040,6 +1055,63 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const __gr
   double* scrD = scrA + (int64_t)(a.L + 1) * 32;
   for (int64_t p0 = gwarp * 32; p0 < a.n_pairs; p0 += nwarps * 32)
     process_batch<kWithK>(a, sm, scrA, scrD, p0, (int)min((int64_t)32, a.n_pairs - p0));
+}
+
+// ------------------------------------------------------------------ single layer: split launch
+// The root kernel runs phases A-C (FP64; lane per pair for the root and the recurrence; no shared
+// memory) and writes one record per pair; the transform kernel runs phase D on the records (double
+// words, shared-memory FFTs).  Each kernel gets its own register and occupancy budget.  Both cover
+// the pairs [c0, c0 + cn) of the launch; the record of pair p is p - c0.
+__global__ void __launch_bounds__(128) pair_root_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int Mt = a.Mt, L = a.L;
+  for (int64_t p0 = c0 + gwarp * 32; p0 < c0 + cn; p0 += nwarps * 32) {
+    const int nb = (int)min((int64_t)32, c0 + cn - p0);
+    const int64_t r0 = p0 - c0;
+    PairInfo mine;
+    unsigned vm;
+    front_batch<false>(a, Smem{}, p0, nb, a.rec_R2 + r0 * Mt, a.rec_E + r0 * 33, a.rec_A + r0 * (L + 1), L + 1, 1,
+                       nullptr, mine, vm);
+    if (lane < nb) {
+      double* h = a.rec_hdr + (r0 + lane) * 8;
+      h[0] = mine.a;
+      h[1] = mine.qb;
+      h[2] = mine.om;
+      h[3] = mine.sha;
+      h[4] = mine.cha;
+      h[5] = mine.valid ? 1.0 : 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
+    pair_transform_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t per_warp = smem_doubles(a.Mt, a.P, a.L, false);
+  const Smem sm = carve(smem + per_warp * wib, a.Mt, a.P, a.L, false);
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int Mt = a.Mt, L = a.L;
+  for (int64_t p0 = c0 + gwarp * 32; p0 < c0 + cn; p0 += nwarps * 32) {
+    const int nb = (int)min((int64_t)32, c0 + cn - p0);
+    const int64_t r0 = p0 - c0;
+    PairInfo mine = {};
+    if (lane < nb) {
+      const double* h = a.rec_hdr + (r0 + lane) * 8;
+      mine.a = h[0];
+      mine.qb = h[1];
+      mine.om = h[2];
+      mine.sha = h[3];
+      mine.cha = h[4];
+      mine.valid = h[5] != 0.0;
+    }
+    const unsigned vm = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
+    phase_d_single(a, sm, reinterpret_cast<const float2*>(a.rec_A + r0 * (L + 1)), L + 1, 1, a.rec_E + r0 * 33,
+                   a.rec_R2 + r0 * Mt, mine, vm, p0, nb);
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -1060,6 +1132,8 @@ struct PairResources {
   int rec_len = 0;
   double* scratch = nullptr;
   size_t scratch_bytes = 0;
+  double* records = nullptr;   // split launch: per-pair records of one chunk
+  size_t records_bytes = 0;
 };
 static PairResources g_res;   // grown on demand (the library drives one device per process)
 
@@ -1124,8 +1198,69 @@ static bie_status ensure_rec(cudaStream_t stream, int L) {
   return BIE_OK;
 }
 
+// pairs per chunk of the split launch (records: (74 + L + 1 + Mt) doubles per pair, 3.5 GB at Mt = 128)
+constexpr int64_t kSplitChunk = 1 << 20;
+
+static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
+  const cudaStream_t st = s->ctx->stream;
+  bie_status rs = ensure_rec(st, a.L);
+  if (rs != BIE_OK) return rs;
+  a.rec = g_res.rec;
+  a.rec_len = g_res.rec_len;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(a.n_pairs, kSplitChunk));
+  const int64_t per_pair = 8 + 2 * 33 + (a.L + 1) + a.Mt;
+  const size_t rbytes = sizeof(double) * (size_t)(per_pair * chunk);
+  cudaError_t e;
+  if (g_res.records_bytes < rbytes) {
+    cudaStreamSynchronize(st);
+    if (g_res.records) cudaFree(g_res.records);
+    g_res.records = nullptr;
+    g_res.records_bytes = 0;
+    e = cudaMalloc((void**)&g_res.records, rbytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pair records)");
+    g_res.records_bytes = rbytes;
+  }
+  a.rec_hdr = g_res.records;
+  a.rec_E = reinterpret_cast<float4*>(g_res.records + 8 * chunk);
+  a.rec_A = g_res.records + (8 + 2 * 33) * chunk;
+  a.rec_R2 = a.rec_A + (a.L + 1) * chunk;
+  // root kernel: register-limited occupancy, no shared memory
+  int per_r = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, pair_root_kernel, 128, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy(pair_root_kernel)");
+  if (per_r < 1) per_r = 1;
+  // transform kernel: the CTA shape (1, 2 or 4 warps) with the most resident warps
+  const size_t per_w = smem_doubles(a.Mt, a.P, a.L, false) * sizeof(double);
+  int wpb = 0, best_w = 0, per_t = 0;
+  for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
+    if (per_w * w > kSmemLimit) continue;
+    if (cudaFuncSetAttribute(pair_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_w * w)) !=
+        cudaSuccess)
+      continue;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_transform_kernel, 32 * w, per_w * w) != cudaSuccess)
+      continue;
+    if (nb * w > best_w) { best_w = nb * w; wpb = w; per_t = nb; }
+  }
+  if (wpb < 1) { set_error("pair transform kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
+  const size_t smem = per_w * wpb;
+  e = cudaFuncSetAttribute(pair_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_transform_kernel)");
+  for (int64_t c0 = 0; c0 < a.n_pairs; c0 += chunk) {
+    const int64_t cn = std::min(chunk, a.n_pairs - c0);
+    const int64_t br = std::max<int64_t>(1, std::min<int64_t>((int64_t)s->ctx->sms * per_r, (cn + 127) / 128));
+    pair_root_kernel<<<(unsigned)br, 128, 0, st>>>(a, c0, cn);
+    const int64_t bt = std::max<int64_t>(1, std::min<int64_t>((int64_t)s->ctx->sms * per_t, (cn + 32 * wpb - 1) / (32 * wpb)));
+    pair_transform_kernel<<<(unsigned)bt, 32 * wpb, smem, st>>>(a, c0, cn);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pair kernels (split launch)");
+  return BIE_OK;
+}
+
 bie_status launch_pairs(bie_surface s, PairArgs& a) {
   const bool withK = a.kernels & BIE_KERNEL_K;
+  if (!withK) return launch_pairs_split(s, a);
   const int wpb = pair_warps_per_block(a.Mt, (unsigned)a.kernels);
   if (wpb < 1) { set_error("pair kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
   const size_t smem = smem_doubles(a.Mt, a.P, a.L, withK) * sizeof(double) * wpb;
