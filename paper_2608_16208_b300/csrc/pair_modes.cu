@@ -329,7 +329,7 @@ __host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK)
   d += withK ? 3 * P : 0;                    // Bcal, VK, VH
   d += withK ? 3 * (L + 1) : 0;              // Atab, Dtab, Btab
   d += 4 * P;                                // W0, W1 (complex)
-  d += 2 * (withK ? 3 : 2) * (2 * M + 1);    // ph, kc (, kk)
+  d += withK ? 2 * 3 * (2 * M + 1) : 2 * (2 * M + 1);   // ph (, kc, kk)
   return d;
 }
 
@@ -345,8 +345,10 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
   s.W0 = (cplx*)p; p += 2 * P;
   s.W1 = (cplx*)p; p += 2 * P;
   s.ph = (cplx*)p; p += 2 * (2 * M + 1);
-  s.kc = (cplx*)p; p += 2 * (2 * M + 1);
-  if (withK) { s.kk = (cplx*)p; p += 2 * (2 * M + 1); }
+  if (withK) {
+    s.kc = (cplx*)p; p += 2 * (2 * M + 1);
+    s.kk = (cplx*)p; p += 2 * (2 * M + 1);
+  }
   return s;
 }
 
@@ -382,8 +384,6 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
   float4* W0 = reinterpret_cast<float4*>(sm.W0);
   float4* W1 = reinterpret_cast<float4*>(sm.W1);
   float2* Acal = reinterpret_cast<float2*>(sm.Acal);
-  float4* ph = reinterpret_cast<float4*>(sm.ph);   // e^{ija} / Mt, j = -M..M
-  float4* kc = reinterpret_cast<float4*>(sm.kc);
   const float2 invMt = dw_from(1.0 / Mt);
   const float2 ratio = dw_from((double)Mt / P);   // e^{ija}/Mt -> e^{ija}/P
   int acal_next = -1;   // pair whose circulant transform already sits in Acal
@@ -398,7 +398,8 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       continue;
     }
     const double* r2p = R2 + pi * Mt;
-    // ---- phases e^{ija}/Mt: lane l starts from e^{i l a}, steps of e^{32 i a}
+    // ---- phases e^{ija}/Mt, j = -M..M: lane l starts from e^{i l a}, steps of e^{32 i a}
+    float4* ph = reinterpret_cast<float4*>(sm.ph);
     {
       float4 e = E[pi * 33 + lane];
       const float4 step = E[pi * 33 + 32];
@@ -409,6 +410,8 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
         e = dwc_mul(e, step);
       }
     }
+    __syncwarp();
+    auto phase = [&](int jj) { return ph[jj]; };   // e^{ija}/Mt, jj = j + M
     // ---- circulant transform of A_{|d|}, unless it came packed with the previous pair
     if (acal_next != pi) {
       for (int pp = lane; pp < P; pp += 32) {
@@ -444,7 +447,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     __syncwarp();
     for (int jj = lane; jj <= 2 * M; jj += 32) {
       const int jv = jj - M;
-      float4 z = dwc_mul(ph[jj], Z1[wrapi(jv, Mt)]);
+      float4 z = dwc_mul(phase(jj), Z1[wrapi(jv, Mt)]);
       if (jv == M || jv == -M) z = dwc_scale2(z, 0.5f);
       X[wrapi(jv, P)] = z;
     }
@@ -484,11 +487,28 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     }
     __syncwarp();
     const float4* Yf = warp_fft_dw(uf, up1, P, a.twf, a.T, -1);
-    // ---- kernel modes kc_m = e^{-ima} Re-part transform / P; the packed circulant transform
-    for (int jj = lane; jj <= 2 * M; jj += 32) {
+    // ---- kernel modes kc_m = e^{-ima} (Re-part transform)_m / P, m = -M..M, written straight to the
+    // modes output and to the free buffer in the input order of the weights' inverse transform
+    // (q = m mod Mt; q = M holds the mean of m = -M and m = M)
+    float4* Wi = (Yf == W0) ? W1 : W0;
+    double* out = a.modes_out ? a.modes_out + p * 2 * (Mt + 1) : nullptr;
+    auto kc_of = [&](int jj) {
       const int m = jj - M;
       const float4 zp = Yf[wrapi(m, P)], zm = dwc_conj(Yf[wrapi(-m, P)]);
-      kc[jj] = dwc_mul(dwc_mulr(dwc_conj(ph[jj]), ratio), dwc_scale2(dwc_add(zp, zm), 0.5f));
+      return dwc_mul(dwc_mulr(dwc_conj(phase(jj)), ratio), dwc_scale2(dwc_add(zp, zm), 0.5f));
+    };
+    for (int jj = lane; jj <= 2 * M; jj += 32) {
+      const float4 kv = kc_of(jj);
+      if (out) {
+        const cplx c = dwc_to(kv);
+        out[2 * jj] = c.re;
+        out[2 * jj + 1] = c.im;
+      }
+      if (a.weights_out) {
+        const int m = jj - M;
+        if (jj == 0) Wi[M] = dwc_scale2(dwc_add(kv, kc_of(2 * M)), 0.5f);
+        else if (jj < 2 * M) Wi[m < 0 ? m + Mt : m] = kv;
+      }
     }
     if (pack) {
       const float unsc = ldexpf(0.5f, -pe);
@@ -499,33 +519,28 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       acal_next = nxt;
     }
     __syncwarp();
-    // ---- outputs: modes K_m = kc_m + i <sin(k rho)/rho>_m, and / or the Parseval weights
-    if (a.modes_out) {
-      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(snw[q], make_float2(0.f, 0.f));
-      __syncwarp();
-      const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
-      double* out = a.modes_out + p * 2 * (Mt + 1);
-      for (int mm = lane; mm <= 2 * M; mm += 32) {
-        const int m = mm - M;
-        cplx sv = dwc_to(Sf[wrapi(m, Mt)]) * (1.0 / Mt);
-        if (m == M || m == -M) sv = 0.5 * sv;
-        const cplx sg = dwc_to(kc[mm]);
-        out[2 * mm] = sg.re - sv.im;
-        out[2 * mm + 1] = sg.im + sv.re;
-      }
-      __syncwarp();
-    }
+    // ---- Parseval weights: inverse transform of the kernel modes, plus sin(k rho)/(rho Mt)
     if (a.weights_out) {
-      for (int q = lane; q < Mt; q += 32) {
-        const int m = q < M ? q : q - Mt;
-        W0[q] = (q == M) ? dwc_scale2(dwc_add(kc[2 * M], kc[0]), 0.5f) : kc[m + M];
-      }
-      __syncwarp();
-      const float4* Wt = warp_fft_dw(W0, W1, Mt, a.twf, a.T, +1);
+      const float4* Wt = warp_fft_dw(Wi, (Wi == W0) ? W1 : W0, Mt, a.twf, a.T, +1);
       cplx* wout = a.weights_out + p * a.w_ld;
       for (int q = lane; q < Mt; q += 32) {
         const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
         wout[q] = C(w.re, w.im + dw_to(snw[q]) * (1.0 / Mt));
+      }
+      __syncwarp();
+    }
+    // ---- modes K_m = kc_m + i <sin(k rho)/rho>_m: the smooth part added to the kernel part in out
+    // (each entry by the lane that wrote it)
+    if (out) {
+      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(snw[q], make_float2(0.f, 0.f));
+      __syncwarp();
+      const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
+      for (int mm = lane; mm <= 2 * M; mm += 32) {
+        const int m = mm - M;
+        cplx sv = dwc_to(Sf[wrapi(m, Mt)]) * (1.0 / Mt);
+        if (m == M || m == -M) sv = 0.5 * sv;
+        out[2 * mm] -= sv.im;
+        out[2 * mm + 1] += sv.re;
       }
       __syncwarp();
     }
