@@ -33,10 +33,12 @@ WORKLOAD = "ellipsoid_np16_m128_k10"
 METRIC = "kernel-mode pairs/s (correction stage, S kernel, FP64)"
 UNIT = "pairs/s"
 FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (profiles/fp64_peak_probe.md)
-# DRAM bytes (read + write) per pair of the pair kernel, from one ncu capture of 75,776 pairs of this
-# workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md), valid only for the kernel source it was
+# DRAM bytes (read + write) per pair of the pair pipeline (root kernel + transform kernel: the kernel
+# modes plus the per-pair records between the two), from one ncu capture of 75,776 pairs of this
+# workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md); valid only for the kernel sources it was
 # taken on: the report carries it while the sources hash to the same value, and null otherwise.
-PAIR_TRAFFIC = {"bytes_per_pair": (68.090624e6 + 292.715776e6) / 75776, "sources": "be4bc295f36c51fe"}
+PAIR_TRAFFIC = {"bytes_per_pair": (10.457344e6 + 298.638592e6 + 245.905408e6 + 123.702272e6) / 75776,
+                "sources": "e44f3ac7b679be2c"}
 
 
 def algorithmic_flops_per_pair(Mt):
@@ -303,7 +305,7 @@ def run_gpu(args):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
-                         "kernel": "pair_kernel<S>", "peak_source": "measured FP64 FMA probe",
+                         "kernel": "pair_root_kernel + pair_transform_kernel (S)", "peak_source": "measured FP64 FMA probe",
                          "traffic_source": "ncu capture of 75,776 pairs, scaled to the %d pairs of a launch" % pk_pairs,
                          "launch_ms": pk_ms,
                          "flops_per_pair": fl, "step_gflops": step_gflops},
