@@ -165,11 +165,16 @@ def pair_kernel_sources_hash():
 
 
 def near_launches(Np, Mt, nk):
-    """Kernel launches of one near-correction pass: the pair pipeline once per group of panels whose
-    weights fit 4 GiB, and the near-band fill once per panel."""
-    per_panel = 16 * (16 * 48 * Mt) * Mt * nk
-    group = max(1, min(Np, (4 << 30) // per_panel))
-    return -(-Np // group) + Np
+    """Kernel launches of one near-correction pass: per group of panels whose weights fit 4 GiB, the
+    pair pipeline (single layer alone: a root and a transform kernel per chunk of 2^20 pairs; with the
+    double layer: one fused kernel), and the near-band fill once per panel."""
+    per_panel_pairs = 16 * 48 * Mt
+    group = max(1, min(Np, (4 << 30) // (16 * per_panel_pairs * Mt * nk)))
+    n = 0
+    for j0 in range(0, Np, group):
+        pairs = per_panel_pairs * min(group, Np - j0)
+        n += 2 * (-(-pairs // (1 << 20))) if nk == 1 else 1
+    return n + Np
 
 
 def run_gpu(args):

@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "bie_internal.cuh"
+#include "dw.cuh"
 #include "pair_args.cuh"
 
 namespace bie {
@@ -69,11 +70,14 @@ __global__ void far_fill_kernel(const FarArgs a) {
 }
 
 // Near fill of one target panel: block per (local target node tl in [0, 16 Mt), delta).
-// A[row, block] += sS * sum_g coef W_S + sK * sum_g coef W_K   (W_K may be null)
+// A[row, block] += sS * sum_g coef W_S + sK * sum_g coef W_K   (W_K may be null).
+// kDW: single layer alone with double-word weights (re.h, re.l, im.h, im.l); the GGQ fold, the
+// scaling and the Jacobian run in double words, and only the update of A in FP64.
+template <bool kDW>
 __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS, cplx sK,
-                                 const double* __restrict__ coef, const cplx* __restrict__ WS,
-                                 const cplx* __restrict__ WK, const double* __restrict__ jcol,
-                                 cplx* __restrict__ A) {
+                                 const double* __restrict__ coef, const float2* __restrict__ coefw,
+                                 const cplx* __restrict__ WS, const cplx* __restrict__ WK,
+                                 const double* __restrict__ jcol, cplx* __restrict__ A) {
   const int tl = blockIdx.x;            // l * Mt + i
   const int d = blockIdx.y;
   const int l = tl / Mt, i = tl % Mt;
@@ -85,6 +89,26 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS,
   const int64_t base = ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
   const double* cf = coef + ((d * 16 + l) * 16) * 16;   // [g][n]
   cplx* Arow = A + row * N + (int64_t)ip * 16 * Mt;
+  if constexpr (kDW) {
+    const float2* cw = coefw + ((d * 16 + l) * 16) * 16;
+    const float4* W = reinterpret_cast<const float4*>(WS);
+    const float4 sw = dwc_from(sS);
+    for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
+      const int n = e / Mt, lp = e % Mt;
+      float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int g = 0; g < 16; ++g) {
+        const float4 w = W[base + (int64_t)g * Mt * Mt + lp];
+        const float2 c = cw[g * 16 + n];
+        ar = dw_add(ar, dw_mul(c, cre(w)));
+        ai = dw_add(ai, dw_mul(c, cim(w)));
+      }
+      float4 add = dwc_mul(sw, mkc(ar, ai));
+      if (jcol) add = dwc_mulr(add, dw_from(jcol[(int64_t)ip * 16 * Mt + e]));   // times J of the source node
+      const cplx ad = dwc_to(add);
+      Arow[e] = Arow[e] + ad;
+    }
+  } else {
   for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
     const int n = e / Mt, lp = e % Mt;
     cplx accS = C(0.0), accK = C(0.0);
@@ -97,6 +121,7 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS,
     cplx add = sS * accS + sK * accK;
     if (jcol) add = jcol[(int64_t)ip * 16 * Mt + e] * add;   // unweighted unknown: times J of the source node
     Arow[e] = Arow[e] + add;
+  }
   }
 }
 
@@ -128,6 +153,7 @@ static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernel
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(weights)");
   bie_status st = BIE_OK;
   const cplx sS = C(ws_re, ws_im) * (0.5 * s->h), sK = C(wk_re, wk_im) * (0.5 * s->h);
+  const bool dw = kernels == BIE_KERNEL_S;   // single layer alone: double-word weights and fold
   for (int j0 = 0; j0 < s->Np && st == BIE_OK; j0 += group) {
     const int nj = (j0 + group <= s->Np) ? group : s->Np - j0;
     PairArgs a = make_pair_args(s, k, kernels);
@@ -136,6 +162,7 @@ static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernel
     a.n_pairs = panel_pairs * nj;
     a.weights_out = W;
     a.weights_stride = panel_pairs * nj * Mt;
+    a.weights_dw = dw;
     st = launch_pairs(s, a);
     if (st != BIE_OK) break;
     const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
@@ -143,9 +170,15 @@ static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernel
     for (int jj = 0; jj < nj; ++jj) {
       const int64_t off = (int64_t)jj * panel_pairs * Mt;
       dim3 grid(16 * Mt, 3);
-      near_fill_kernel<<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
-                                                       WS ? WS + off : nullptr, WK ? WK + off : nullptr,
-                                                       unweighted ? s->jac : nullptr, (cplx*)A_out);
+      if (dw)
+        near_fill_kernel<true><<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
+                                                              s->near_coef_dw, WS + off, nullptr,
+                                                              unweighted ? s->jac : nullptr, (cplx*)A_out);
+      else
+        near_fill_kernel<false><<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
+                                                               s->near_coef_dw, WS ? WS + off : nullptr,
+                                                               WK ? WK + off : nullptr,
+                                                               unweighted ? s->jac : nullptr, (cplx*)A_out);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");

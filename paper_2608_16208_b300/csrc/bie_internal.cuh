@@ -332,6 +332,7 @@ struct bie_surface_s {
   double* ring_r;      // [dev] [n_rings][Mt][3]
   double* ring_n;      // [dev] [n_rings][Mt][3]
   double* near_coef;   // [dev] [3][16][16][16] = w_g L_n(x_g) on the reference panel
+  float2* near_coef_dw;  // [dev] the same as double words
   double* ggq_x;       // [dev] [3][16][16]
   bie::cplx* tw;       // [dev] twiddles for length 12 Mt
   float4* twf;         // [dev] the same twiddles as double words (re.h, re.l, im.h, im.l)

@@ -272,7 +272,8 @@ __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restr
     up = cur;
     cur = prev;
     if (m - 1 <= L) A[(m - 1) * stride] = cur;
-    if (fabs(cur) > 1e200) {
+    // |A~| grows by at most 4 cosh(b) <= 4 cosh 4 per step: checking every 8 steps keeps it below 1e215
+    if ((m & 7) == 0 && fabs(cur) > 1e200) {
       cur *= 1e-200;
       up *= 1e-200;
       for (int j = m - 1; j <= L; ++j) A[j * stride] *= 1e-200;
@@ -523,9 +524,17 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     if (a.weights_out) {
       const float4* Wt = warp_fft_dw(Wi, (Wi == W0) ? W1 : W0, Mt, a.twf, a.T, +1);
       cplx* wout = a.weights_out + p * a.w_ld;
-      for (int q = lane; q < Mt; q += 32) {
-        const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
-        wout[q] = C(w.re, w.im + dw_to(snw[q]) * (1.0 / Mt));
+      if (a.weights_dw) {
+        float4* wo = reinterpret_cast<float4*>(wout);
+        for (int q = lane; q < Mt; q += 32) {
+          const float4 w = Wt[q];
+          wo[q] = mkc(dw_mul(cre(w), invMt), dw_mul(dw_add(cim(w), snw[q]), invMt));
+        }
+      } else {
+        for (int q = lane; q < Mt; q += 32) {
+          const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
+          wout[q] = C(w.re, w.im + dw_to(snw[q]) * (1.0 / Mt));
+        }
       }
       __syncwarp();
     }
@@ -608,11 +617,15 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
       const double* rr = a.ring_r + pr.ring * 3 * Mt;
       const int i = (int)(pr.row % Mt);
       const double dts = fabs(pr.t - pr.ts);
+      // |t - t_s| + |th_i - th_q| <= kStableDelta as a bound on the grid distance |i - q| (both
+      // branches give rho^2 to rounding, so the boundary only picks the cheaper formula)
+      const int kn = dts <= kStableDelta ? (int)((kStableDelta - dts) * Mt / kTwoPi) : -1;
       double bv = INFINITY;
       for (int q = lane; q < Mt; q += 32) {
         const double thq = a.thg[3 * q];
+        const int dq = q > i ? q - i : i - q;
         double r2;
-        if (dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta) {
+        if (min(dq, Mt - dq) <= kn) {
           const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
           r2 = dot(Y, Y);
         } else {
@@ -625,8 +638,9 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
       for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
       __syncwarp();
       int bkey = 0x7fffffff;
+      const double tie = bv * (1 + 1e-12);
       for (int q = lane; q < Mt; q += 32)
-        if (rho2[q] <= bv * (1 + 1e-12)) {
+        if (rho2[q] <= tie) {
           const int dq = q > i ? q - i : i - q;
           bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
         }

@@ -142,6 +142,11 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
           coef[((d * 16 + l) * 16 + g) * 16 + n] = ggq->w[d][l][g] * Ln;
         }
       }
+  std::vector<float2> coefw(coef.size());   // the same as double words
+  for (size_t e = 0; e < coef.size(); ++e) {
+    const float h = (float)coef[e];
+    coefw[e] = make_float2(h, (float)(coef[e] - (double)h));
+  }
   // twiddles for length 12 Mt
   const int T = 12 * Mt;
   std::vector<cplx> tw(T);
@@ -176,6 +181,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   ALLOC(s->ring_r, sizeof(double) * 3 * s->n_rings * Mt);
   ALLOC(s->ring_n, sizeof(double) * 3 * s->n_rings * Mt);
   ALLOC(s->near_coef, sizeof(double) * coef.size());
+  ALLOC(s->near_coef_dw, sizeof(float2) * coef.size());
   ALLOC(s->ggq_x, sizeof(double) * 3 * 16 * 16);
   ALLOC(s->tw, sizeof(cplx) * T);
   ALLOC(s->twf, sizeof(float4) * T);
@@ -188,6 +194,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   H2D(s->t_nodes, tn.data(), sizeof(double) * 16 * Np);
   H2D(s->ring_t, rt.data(), sizeof(double) * s->n_rings);
   H2D(s->near_coef, coef.data(), sizeof(double) * coef.size());
+  H2D(s->near_coef_dw, coefw.data(), sizeof(float2) * coefw.size());
   H2D(s->ggq_x, &ggq->x[0][0][0], sizeof(double) * 3 * 16 * 16);
   H2D(s->tw, tw.data(), sizeof(cplx) * T);
   H2D(s->twf, twf.data(), sizeof(float4) * T);
@@ -210,7 +217,7 @@ void bie_surface_free(bie_surface s) {
   if (!s) return;
   cudaFree(s->t_nodes); cudaFree(s->pts); cudaFree(s->nrm); cudaFree(s->jac);
   cudaFree(s->ring_t); cudaFree(s->ring_r); cudaFree(s->ring_n);
-  cudaFree(s->near_coef); cudaFree(s->ggq_x); cudaFree(s->tw); cudaFree(s->twf); cudaFree(s->thgrid);
+  cudaFree(s->near_coef); cudaFree(s->near_coef_dw); cudaFree(s->ggq_x); cudaFree(s->tw); cudaFree(s->twf); cudaFree(s->thgrid);
   delete[] s->host_t_nodes;
   delete s;
 }
