@@ -169,6 +169,14 @@ __device__ __forceinline__ float4 mul_i(float4 a, int sign) {   // sign * i * a
   return sign < 0 ? make_float4(a.z, a.w, -a.x, -a.y) : make_float4(-a.z, -a.w, a.x, a.y);
 }
 
+// j = q Ns + jm: by shift and mask when Ns is a power of two (every stage of the power-of-two
+// plans), by division otherwise
+struct StageIdx {
+  int Ns, sh;   // sh >= 0: Ns = 2^sh
+  __device__ __forceinline__ int rem(int j) const { return sh >= 0 ? (j & (Ns - 1)) : j % Ns; }
+  __device__ __forceinline__ int quo(int j) const { return sh >= 0 ? (j >> sh) : j / Ns; }
+};
+
 static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, const float4* __restrict__ tw, int T,
                                                    int sign) {
   const int lane = threadIdx.x & 31;
@@ -182,9 +190,10 @@ static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, 
     const int R = p.rad[st];
     const int stride = n / R;
     const int tstep = (T / n) * (n / (Ns * R));   // r * jm * tstep < T
+    const StageIdx ix = {Ns, (Ns & (Ns - 1)) == 0 ? __ffs(Ns) - 1 : -1};
     if (R == 4) {
       for (int j = lane; j < stride; j += 32) {
-        const int jm = j % Ns;
+        const int jm = ix.rem(j);
         float4 v0 = src[j], v1 = src[j + stride], v2 = src[j + 2 * stride], v3 = src[j + 3 * stride];
         if (jm) {
           v1 = dwc_mul(v1, tw_load(tw, jm * tstep, sign));
@@ -193,7 +202,7 @@ static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, 
         }
         const float4 s02 = dwc_add(v0, v2), d02 = dwc_sub(v0, v2), s13 = dwc_add(v1, v3);
         const float4 jd = mul_i(dwc_sub(v1, v3), sign);
-        const int idx = (j / Ns) * Ns * 4 + jm;
+        const int idx = ix.quo(j) * Ns * 4 + jm;
         dst[idx] = dwc_add(s02, s13);
         dst[idx + Ns] = dwc_add(d02, jd);
         dst[idx + 2 * Ns] = dwc_sub(s02, s13);
@@ -201,17 +210,17 @@ static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, 
       }
     } else if (R == 2) {
       for (int j = lane; j < stride; j += 32) {
-        const int jm = j % Ns;
+        const int jm = ix.rem(j);
         const float4 v0 = src[j];
         float4 v1 = src[j + stride];
         if (jm) v1 = dwc_mul(v1, tw_load(tw, jm * tstep, sign));
-        const int idx = (j / Ns) * Ns * 2 + jm;
+        const int idx = ix.quo(j) * Ns * 2 + jm;
         dst[idx] = dwc_add(v0, v1);
         dst[idx + Ns] = dwc_sub(v0, v1);
       }
     } else {
       for (int j = lane; j < stride; j += 32) {
-        const int jm = j % Ns;
+        const int jm = ix.rem(j);
         const float4 v0 = src[j];
         float4 v1 = src[j + stride], v2 = src[j + 2 * stride];
         if (jm) {
@@ -222,7 +231,7 @@ static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, 
         // t2 = s3 * i * d (s3 carries the sign)
         const float4 t2 = mkc(dw_neg(dw_mul(s3, cim(d))), dw_mul(s3, cre(d)));
         const float4 base = dwc_sub(v0, dwc_scale2(t1, 0.5f));
-        const int idx = (j / Ns) * Ns * 3 + jm;
+        const int idx = ix.quo(j) * Ns * 3 + jm;
         dst[idx] = dwc_add(v0, t1);
         dst[idx + Ns] = dwc_add(base, t2);
         dst[idx + 2 * Ns] = dwc_sub(base, t2);

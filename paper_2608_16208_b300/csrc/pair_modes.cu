@@ -297,6 +297,8 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
+// v mod n for |v| < n
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // sin(k x) - k sin(x), k >= 0, without cancellation (series when k x < 1).
 __device__ inline double sin_k_minus(int k, double x) {
@@ -448,9 +450,9 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     __syncwarp();
     for (int jj = lane; jj <= 2 * M; jj += 32) {
       const int jv = jj - M;
-      float4 z = dwc_mul(phase(jj), Z1[wrapi(jv, Mt)]);
+      float4 z = dwc_mul(phase(jj), Z1[wrap1(jv, Mt)]);
       if (jv == M || jv == -M) z = dwc_scale2(z, 0.5f);
-      X[wrapi(jv, P)] = z;
+      X[wrap1(jv, P)] = z;
     }
     __syncwarp();
     float4* up1 = warp_fft_dw(X, Z1, P, a.twf, a.T, +1);   // re: F~, im: C~
@@ -495,7 +497,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     double* out = a.modes_out ? a.modes_out + p * 2 * (Mt + 1) : nullptr;
     auto kc_of = [&](int jj) {
       const int m = jj - M;
-      const float4 zp = Yf[wrapi(m, P)], zm = dwc_conj(Yf[wrapi(-m, P)]);
+      const float4 zp = Yf[wrap1(m, P)], zm = dwc_conj(Yf[wrap1(-m, P)]);
       return dwc_mul(dwc_mulr(dwc_conj(phase(jj)), ratio), dwc_scale2(dwc_add(zp, zm), 0.5f));
     };
     for (int jj = lane; jj <= 2 * M; jj += 32) {
@@ -514,7 +516,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     if (pack) {
       const float unsc = ldexpf(0.5f, -pe);
       for (int pp = lane; pp < P; pp += 32) {
-        const float4 zp = Yf[pp], zm = dwc_conj(Yf[(P - pp) % P]);
+        const float4 zp = Yf[pp], zm = dwc_conj(Yf[pp == 0 ? 0 : P - pp]);
         Acal[pp] = dw_scale2(dw_sub(cim(zp), cim(zm)), unsc);
       }
       acal_next = nxt;
@@ -546,7 +548,7 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
       for (int mm = lane; mm <= 2 * M; mm += 32) {
         const int m = mm - M;
-        cplx sv = dwc_to(Sf[wrapi(m, Mt)]) * (1.0 / Mt);
+        cplx sv = dwc_to(Sf[wrap1(m, Mt)]) * (1.0 / Mt);
         if (m == M || m == -M) sv = 0.5 * sv;
         out[2 * mm] -= sv.im;
         out[2 * mm + 1] += sv.re;
