@@ -247,7 +247,18 @@ def run_gpu(args):
     torch.cuda.synchronize()
     pk_ms = float(np.mean([a.elapsed_time(b) for a, b in pk_events]))
     pk_pairs = rows_all.numel()
-    del modes, rows_all, srcs_all, panel, keep
+    del modes
+    # the single and double layer together over the same pairs (fused FP64 kernel), reported apart
+    modes_sk = torch.empty((rows_all.numel(), 2, Mt + 1), dtype=torch.complex128, device=dev)
+    bie.kernel_modes(surf, bie.KERNEL_S | bie.KERNEL_K, k, rows_all, srcs_all, out=modes_sk)
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bie.kernel_modes(surf, bie.KERNEL_S | bie.KERNEL_K, k, rows_all, srcs_all, out=modes_sk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sk_ms = e0.elapsed_time(e1)
+    del modes_sk, rows_all, srcs_all, panel, keep
     fl = algorithmic_flops_per_pair(Mt)
     traffic = (PAIR_TRAFFIC["bytes_per_pair"] * pk_pairs
                if pair_kernel_sources_hash() == PAIR_TRAFFIC["sources"] else None)
@@ -320,6 +331,8 @@ def run_gpu(args):
                              "sample": "%d near pairs of 400 seeded target rows, method mode, %.1f s" % (cpu_n, cpu_dt)},
             "solve": solve,
             "batch": batch,
+            "single_and_double_layer": {"pairs_per_s": pk_pairs / (sk_ms / 1000.0), "ms": sk_ms, "pairs": pk_pairs,
+                                        "kernels": "S+K", "path": "fused FP64 pair kernel"},
         }
         print(json.dumps(line))
     if world > 1:
