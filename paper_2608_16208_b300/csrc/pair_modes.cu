@@ -331,6 +331,7 @@ __host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK)
   d += P;                                    // Acal
   d += withK ? 3 * P : 0;                    // Bcal, VK, VH
   d += withK ? 3 * (L + 1) : 0;              // Atab, Dtab, Btab
+  d += d & 1;                                // W0, W1 start on 16 bytes: the transforms read float4
   d += 4 * P;                                // W0, W1 (complex)
   d += withK ? 2 * 3 * (2 * M + 1) : 2 * (2 * M + 1);   // ph (, kc, kk)
   return d;
@@ -345,6 +346,7 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
   s.Acal = p; p += P;
   if (withK) { s.Bcal = p; p += P; s.VK = p; p += P; s.VH = p; p += P; }
   if (withK) { s.Atab = p; p += L + 1; s.Dtab = p; p += L + 1; s.Btab = p; p += L + 1; }
+  p += (p - base) & 1;   // 16-byte start for the double-word transforms
   s.W0 = (cplx*)p; p += 2 * P;
   s.W1 = (cplx*)p; p += 2 * P;
   s.ph = (cplx*)p; p += 2 * (2 * M + 1);
@@ -355,10 +357,30 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
   return s;
 }
 
+// Transform of complex doubles (warp_fft's contract) through the double-word FFT: convert in place,
+// transform, convert the result back (integer splits, one FP64 add per component on the way back).
+__device__ __noinline__ cplx* warp_fft_x(cplx* x, cplx* y, int n, const float4* __restrict__ twf, int T, int sign) {
+  const int lane = threadIdx.x & 31;
+  float4* xf = reinterpret_cast<float4*>(x);
+  for (int i = lane; i < n; i += 32) {
+    const cplx v = x[i];
+    xf[i] = dwc_from(v);
+  }
+  __syncwarp();
+  float4* r = warp_fft_dw(xf, reinterpret_cast<float4*>(y), n, twf, T, sign);
+  cplx* rc = reinterpret_cast<cplx*>(r);
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = r[i];
+    rc[i] = dwc_to(v);
+  }
+  __syncwarp();
+  return rc;
+}
+
 // e^{ija} Z_j / Mt (j = -M..M, Nyquist split evenly) placed on the P grid in X, inverse
-// transform with scratch Y; returns the buffer holding the result.
+// transform with scratch Y (in double words if dw); returns the buffer holding the result.
 __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y, int Mt, int P, const cplx* tw,
-                                 int T) {
+                                 const float4* twf, int T, bool dw) {
   const int lane = threadIdx.x & 31;
   const int M = Mt / 2;
   for (int pp = lane; pp < P; pp += 32) X[pp] = C(0.0);
@@ -370,7 +392,7 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
     X[wrapi(jv, P)] = ph[jj] * z;
   }
   __syncwarp();
-  return warp_fft(X, Y, P, tw, T, +1);
+  return dw ? warp_fft_x(X, Y, P, twf, T, +1) : warp_fft(X, Y, P, tw, T, +1);
 }
 
 // ------------------------------------------------------------------ phase D, single layer alone
@@ -691,6 +713,10 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       phase_d_single(a, sm, reinterpret_cast<const float2*>(scrA), 1, 32, reinterpret_cast<const float4*>(scrD), R2, mine, valid_mask, p0, nb);
     } else {
     // ---------------- D. per pair (warp)
+    // The transforms this layer shares with the single layer (the samples F + i cos, their
+    // upsampling, the S product, the outputs) run in double words; those of the double layer stay
+    // FP64: they pack signals of very different size (tau_0 ~ curvature rho^2 beside alpha ~ k^2,
+    // A beside B, V_K A~ beside V_H), and extracting the small one costs digits in proportion.
     int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = bcast(mine, pi);
@@ -851,7 +877,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         __syncwarp();
       }
       // ---- D4. S: FFT of F + i cos(k rho), upsample, Toeplitz with A
-      cplx* Z1 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+      cplx* Z1 = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
       cplx* Zf = (Z1 == sm.W0) ? sm.W1 : sm.W0;
       double dFa = 0.0;   // F'(a) from the interpolant of F (well conditioned, unlike the direct form)
       if (translated) {
@@ -866,7 +892,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         }
         dFa = warp_sum(acc);
       }
-      cplx* up1 = upsample(Z1, sm.ph, Zf, Z1, Mt, P, a.tw, a.T);   // re: F~, im: C~
+      cplx* up1 = upsample(Z1, sm.ph, Zf, Z1, Mt, P, a.tw, a.twf, a.T, true);   // re: F~, im: C~
       cplx* uf = (up1 == sm.W0) ? sm.W1 : sm.W0;
       if (wantK)
         for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up1[pp].re;   // keep F~ for V_K
@@ -882,7 +908,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], an);
         }
         __syncwarp();
-        const cplx* Yf = warp_fft(uf, up1, P, a.tw, a.T, -1);
+        const cplx* Yf = warp_fft_x(uf, up1, P, a.twf, a.T, -1);
         for (int jj = lane; jj <= 2 * M; jj += 32) {
           const int m = jj - M;
           const cplx zp = Yf[wrapi(m, P)], zm = conj(Yf[wrapi(-m, P)]);
@@ -900,7 +926,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       } else if (wantS) {
         for (int pp = lane; pp < P; pp += 32) uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], 0.0);
         __syncwarp();
-        const cplx* Yf = warp_fft(uf, up1, P, a.tw, a.T, -1);
+        const cplx* Yf = warp_fft_x(uf, up1, P, a.twf, a.T, -1);
         for (int jj = lane; jj <= 2 * M; jj += 32) sm.kc[jj] = conj(sm.ph[jj]) * Yf[wrapi(jj - M, P)] * (1.0 / P);
       }
       __syncwarp();
@@ -910,7 +936,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         __syncwarp();
         cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
         cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
-        cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.T);   // re: tau0~, im: alpha~
+        cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.twf, a.T, false);   // re: tau0~, im: alpha~
         for (int pp = lane; pp < P; pp += 32) sm.VK[pp] = up2[pp].re * up2[pp].im * sm.VH[pp];
         __syncwarp();
         // ---- D6. H3 modes (symmetric), with beta tau_0 packed in the imaginary part
@@ -1041,7 +1067,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         if (a.modes_out) {
           for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(isS ? sm.sn[q] : sm.bt0[q], 0.0);
           __syncwarp();
-          const cplx* Sf = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+          const cplx* Sf = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
           double* out = a.modes_out + (p * nk + kidx) * 2 * (Mt + 1);
           for (int mm = lane; mm <= 2 * M; mm += 32) {
             const int m = mm - M;
@@ -1059,7 +1085,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
             sm.W0[q] = (q == M) ? 0.5 * (sing[2 * M] + sing[0]) : sing[m + M];
           }
           __syncwarp();
-          const cplx* Wt = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, +1);
+          const cplx* Wt = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, +1);
           cplx* wout = a.weights_out + kidx * a.weights_stride + p * a.w_ld;
           for (int q = lane; q < Mt; q += 32) {
             const cplx w = Wt[q] * (1.0 / Mt);
