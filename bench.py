@@ -37,8 +37,8 @@ FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (pr
 # modes plus the per-pair records between the two), from one ncu capture of 75,776 pairs of this
 # workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md); valid only for the kernel sources it was
 # taken on: the report carries it while the sources hash to the same value, and null otherwise.
-PAIR_TRAFFIC = {"bytes_per_pair": (10.457344e6 + 298.638592e6 + 245.905408e6 + 123.702272e6) / 75776,
-                "sources": "e44f3ac7b679be2c"}
+PAIR_TRAFFIC = {"bytes_per_pair": (11.171584e6 + 296.974080e6 + 245.893632e6 + 123.251200e6) / 75776,
+                "sources": "bd31a062f1086f98"}
 
 
 def algorithmic_flops_per_pair(Mt):
