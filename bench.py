@@ -164,6 +164,19 @@ def pair_kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
+def job_throughput(step_ms, units_per_rank, world, device=None):
+    """Whole-job rate of `world` replicas that each processed units_per_rank in their own step time:
+    the job takes the slowest rank's time (max over ranks, one all_reduce when world > 1).
+    Returns (job step time in ms, units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(step_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    return step_ms, world * units_per_rank / (step_ms / 1000.0)
+
+
 def near_launches(Np, Mt, nk):
     """Kernel launches of one near-correction pass: per group of panels whose weights fit 4 GiB, the
     pair pipeline (single layer alone: a root and a transform kernel per chunk of 2^20 pairs; with the
@@ -219,13 +232,8 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     ms = [e0.elapsed_time(e1) for e0, e1 in events]
-    step_ms = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
     pairs = surf.near_pairs
-    value = world * pairs / (step_ms / 1000.0)
+    step_ms, value = job_throughput(float(np.mean(ms)), pairs, world, dev)
     launches_per_step = near_launches(Np, Mt, 1)
 
     # dominant kernel: the pair pipeline over every near pair of the surface in one launch (the
