@@ -212,6 +212,26 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
 bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
                              double ws_re, double ws_im, double wk_re, double wk_im, double* A_out);
 
+/* Correction stage into the near band alone (Section 3.4): the same entries
+ * as bie_assemble_near adds to a zero matrix, in the band layout
+ *   band_out double2[N][3][16*Mth]:  row = target node index,
+ *   slot d = (source panel) - (target panel) + 1, entry = column within that
+ *   source panel (Legendre node n, theta index) = n*Mth + theta.
+ * Slots of source panels outside the surface (d = 0 on the first panel,
+ * d = 2 on the last) are zero.  Every entry is overwritten.
+ * band_out is either device memory (written in place) or page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister): then the band is filled on the
+ * device a group of target panels at a time in two staging slots
+ * (2 * group * 16*Mth rows, freed on return, stream-ordered) and each group is
+ * copied to the host on a second stream while the next group's pair kernels
+ * run.  Asynchronous on the ctx stream either way: the band is complete once
+ * the ctx stream passes this call (bie_ctx_sync).  Pageable host memory is
+ * refused (BIE_EINVAL).  The caller keeps the buffer alive until then.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.                                  */
+bie_status bie_assemble_near_band(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                                  double ws_re, double ws_im, double wk_re, double wk_im,
+                                  double* band_out);
+
 /* ---- block-diagonal preconditioner ------------------------------------------
  * LU factors, with partial pivoting, of the n / block diagonal blocks
  * A[b block : (b+1) block, same] of the system matrix.  With block = 16 Mth

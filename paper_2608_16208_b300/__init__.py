@@ -177,6 +177,7 @@ def kernel_modes(surface, kernels, k, rows, srcs, out=None):
 
 _sig("bie_assemble", _i32, [_vp, _vp, _i32, _d, _d, _vp])
 _sig("bie_assemble_near", _i32, [_vp, _vp, _u, _d, _d, _d, _d, _d, _vp])
+_sig("bie_assemble_near_band", _i32, [_vp, _vp, _u, _d, _d, _d, _d, _d, _vp])
 _sig("bie_solve", _i32, [_vp, _i64, _vp, _vp, _i32, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)])
 _sig("bie_rhs", _i32, [_vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _d, _vp])
 _sig("bie_field_eval", _i32, [_vp, _vp, _i32, _d, _d, _vp, _vp, _i64, _i32, _vp])
@@ -198,6 +199,23 @@ def assemble_near(surface, kernels, k, A, ws=1.0, wk=0.0):
     check(lib.bie_assemble_near(surface.ctx.h, surface.h, kernels, float(k), ws.real, ws.imag, wk.real, wk.imag,
                                 _ptr(A)), "bie_assemble_near")
     return A
+
+
+def assemble_near_band(surface, kernels, k, out=None, ws=1.0, wk=0.0, host=False):
+    """Near band of ws * S + wk * K: complex128 [N, 3, 16 Mt] (slot d = source panel - target panel + 1).
+
+    out: a device tensor, or a page-locked host tensor (host=True allocates one); with host memory the
+    copies of finished panel groups overlap the pair kernels of the next.  Complete after ctx.sync()."""
+    ws, wk = complex(ws), complex(wk)
+    shape = (surface.N, 3, 16 * surface.Mt)
+    if out is None:
+        out = (torch.empty(shape, dtype=torch.complex128, pin_memory=True) if host
+               else torch.empty(shape, dtype=torch.complex128, device="cuda"))
+    if tuple(out.shape) != shape or out.dtype != torch.complex128 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous complex128 tensor of shape %s" % (shape,))
+    check(lib.bie_assemble_near_band(surface.ctx.h, surface.h, kernels, float(k), ws.real, ws.imag, wk.real,
+                                     wk.imag, _ptr(out)), "bie_assemble_near_band")
+    return out
 
 
 def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,

@@ -69,26 +69,41 @@ __global__ void far_fill_kernel(const FarArgs a) {
   }
 }
 
+// Where the near fill writes: the dense matrix (row-major, leading dimension N, entries added
+// to what is there), or the near band (row - row0, leading dimension 3*16*Mt, slot delta of
+// 16*Mt entries per row; entries overwritten, slots of source panels outside the surface zeroed).
+struct NearOut {
+  cplx* A;
+  int64_t ld, row0;
+  int band;
+};
+
 // Near fill of one target panel: block per (local target node tl in [0, 16 Mt), delta).
 // A[row, block] += sS * sum_g coef W_S + sK * sum_g coef W_K   (W_K may be null).
 // kDW: single layer alone with double-word weights (re.h, re.l, im.h, im.l); the GGQ fold, the
 // scaling and the Jacobian run in double words, and only the update of A in FP64.
 template <bool kDW>
-__global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS, cplx sK,
+__global__ void near_fill_kernel(int Np, int Mt, int jpanel, cplx sS, cplx sK,
                                  const double* __restrict__ coef, const float2* __restrict__ coefw,
                                  const cplx* __restrict__ WS, const cplx* __restrict__ WK,
-                                 const double* __restrict__ jcol, cplx* __restrict__ A) {
+                                 const double* __restrict__ jcol, const NearOut out) {
   const int tl = blockIdx.x;            // l * Mt + i
   const int d = blockIdx.y;
   const int l = tl / Mt, i = tl % Mt;
   const int ip = jpanel + d - 1;
-  if (ip < 0 || ip >= Np) return;
+  const bool inside = ip >= 0 && ip < Np;
+  if (!inside && !out.band) return;
   const int64_t tn = (int64_t)jpanel * 16 + l;
   const int64_t row = tn * Mt + i;
+  cplx* Arow = out.band ? out.A + (row - out.row0) * out.ld + (int64_t)d * 16 * Mt
+                        : out.A + row * out.ld + (int64_t)ip * 16 * Mt;
+  if (!inside) {
+    for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) Arow[e] = C(0.0);
+    return;
+  }
   // weight index within the panel chunk: (((l*3 + d)*16 + g)*Mt + i)
   const int64_t base = ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
   const double* cf = coef + ((d * 16 + l) * 16) * 16;   // [g][n]
-  cplx* Arow = A + row * N + (int64_t)ip * 16 * Mt;
   if constexpr (kDW) {
     const float2* cw = coefw + ((d * 16 + l) * 16) * 16;
     const float4* W = reinterpret_cast<const float4*>(WS);
@@ -106,7 +121,7 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS,
       float4 add = dwc_mul(sw, mkc(ar, ai));
       if (jcol) add = dwc_mulr(add, dw_from(jcol[(int64_t)ip * 16 * Mt + e]));   // times J of the source node
       const cplx ad = dwc_to(add);
-      Arow[e] = Arow[e] + ad;
+      Arow[e] = out.band ? ad : Arow[e] + ad;
     }
   } else {
   for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
@@ -120,7 +135,7 @@ __global__ void near_fill_kernel(int Np, int Mt, int64_t N, int jpanel, cplx sS,
     }
     cplx add = sS * accS + sK * accK;
     if (jcol) add = jcol[(int64_t)ip * 16 * Mt + e] * add;   // unweighted unknown: times J of the source node
-    Arow[e] = Arow[e] + add;
+    Arow[e] = out.band ? add : Arow[e] + add;
   }
   }
 }
@@ -131,31 +146,59 @@ using namespace bie;
 
 extern "C" {
 
-static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re,
-                                     double ws_im, double wk_re, double wk_im, double* A_out, bool unweighted) {
-  if (!ctx || !s || !A_out) { set_error("bie_assemble_near: NULL argument"); return BIE_EINVAL; }
-  if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble_near: k must be in (0, 1e6)"); return BIE_EINVAL; }
-  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
-    set_error("bie_assemble_near: bad kernel mask %u", kernels);
-    return BIE_EINVAL;
-  }
+// Correction stage over all target panels, in groups of panels whose pair weights fit a ~4 GB
+// buffer.  dst: where the near fill writes (NearOut; row0 is set per group when staging).
+// host_band: page-locked host memory for the near band [N][3][16 Mt]; the fill then writes two
+// device staging slots of one group's band rows each, and the copy of a finished group to the
+// host runs on a second stream while the next group's pair kernels run.  The ctx stream waits for
+// the last copy, so the band is complete when the ctx stream reaches the end of this call.
+static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, double k, cplx ws, cplx wk,
+                             const double* jac, NearOut dst, cplx* host_band) {
   const int Mt = s->Mt;
   const int nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + ((kernels & BIE_KERNEL_K) ? 1 : 0);
   const int64_t panel_pairs = (int64_t)16 * 48 * Mt;
+  const int64_t panel_rows = (int64_t)16 * Mt;
   // panels per launch: enough pairs for many waves, weight buffer at most ~4 GB
   const size_t per_panel_bytes = sizeof(cplx) * (size_t)panel_pairs * Mt * nk;
   int group = (int)(((size_t)4 << 30) / per_panel_bytes);
   if (group < 1) group = 1;
   if (group > s->Np) group = s->Np;
+  if (host_band && group > (s->Np + 3) / 4) group = (s->Np + 3) / 4;   // >= 4 groups: copies overlap compute
   const int64_t chunk_pairs = panel_pairs * group;
+  const cudaStream_t st0 = ctx->stream;
   cplx* W = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt * nk, ctx->stream);
+  cudaError_t e = cudaMallocAsync((void**)&W, sizeof(cplx) * chunk_pairs * Mt * nk, st0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(weights)");
+  cplx* stage = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_fill[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+  const int64_t slot_elems = (int64_t)group * panel_rows * dst.ld;
   bie_status st = BIE_OK;
-  const cplx sS = C(ws_re, ws_im) * (0.5 * s->h), sK = C(wk_re, wk_im) * (0.5 * s->h);
+  if (host_band) {
+    e = cudaMallocAsync((void**)&stage, sizeof(cplx) * 2 * slot_elems, st0);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMallocAsync(band staging)");
+    if (st == BIE_OK && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+      st = cuda_fail(e, "cudaStreamCreate(band copies)");
+    for (int q = 0; q < 2 && st == BIE_OK; ++q) {
+      if ((e = cudaEventCreateWithFlags(&ev_fill[q], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ev_copy[q], cudaEventDisableTiming)) != cudaSuccess)
+        st = cuda_fail(e, "cudaEventCreate(band copies)");
+    }
+  }
+  const cplx sS = ws * (0.5 * s->h), sK = wk * (0.5 * s->h);
   const bool dw = kernels == BIE_KERNEL_S;   // single layer alone: double-word weights and fold
-  for (int j0 = 0; j0 < s->Np && st == BIE_OK; j0 += group) {
+  for (int j0 = 0, gi = 0; j0 < s->Np && st == BIE_OK; j0 += group, ++gi) {
     const int nj = (j0 + group <= s->Np) ? group : s->Np - j0;
+    const int slot = gi & 1;
+    NearOut o = dst;
+    if (host_band) {
+      if (gi >= 2 && (e = cudaStreamWaitEvent(st0, ev_copy[slot], 0)) != cudaSuccess) {
+        st = cuda_fail(e, "cudaStreamWaitEvent(band slot)");
+        break;
+      }
+      o.A = stage + slot * slot_elems;
+      o.row0 = (int64_t)j0 * panel_rows;
+    }
     PairArgs a = make_pair_args(s, k, kernels);
     a.enumerate = 1;
     a.p0 = (int64_t)j0 * panel_pairs;
@@ -171,25 +214,78 @@ static bie_status assemble_near_impl(bie_ctx ctx, bie_surface s, unsigned kernel
       const int64_t off = (int64_t)jj * panel_pairs * Mt;
       dim3 grid(16 * Mt, 3);
       if (dw)
-        near_fill_kernel<true><<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
-                                                              s->near_coef_dw, WS + off, nullptr,
-                                                              unweighted ? s->jac : nullptr, (cplx*)A_out);
+        near_fill_kernel<true><<<grid, 256, 0, st0>>>(s->Np, Mt, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
+                                                      WS + off, nullptr, jac, o);
       else
-        near_fill_kernel<false><<<grid, 256, 0, ctx->stream>>>(s->Np, Mt, s->N, j0 + jj, sS, sK, s->near_coef,
-                                                               s->near_coef_dw, WS ? WS + off : nullptr,
-                                                               WK ? WK + off : nullptr,
-                                                               unweighted ? s->jac : nullptr, (cplx*)A_out);
+        near_fill_kernel<false><<<grid, 256, 0, st0>>>(s->Np, Mt, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
+                                                       WS ? WS + off : nullptr, WK ? WK + off : nullptr, jac, o);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_fail(e, "near_fill_kernel");
+    if (e != cudaSuccess) { st = cuda_fail(e, "near_fill_kernel"); break; }
+    if (host_band) {
+      if ((e = cudaEventRecord(ev_fill[slot], st0)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(cs, ev_fill[slot], 0)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(host_band + o.row0 * dst.ld, o.A, sizeof(cplx) * nj * panel_rows * dst.ld,
+                               cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+          (e = cudaEventRecord(ev_copy[slot], cs)) != cudaSuccess)
+        st = cuda_fail(e, "near band copy to the host");
+    }
   }
-  cudaFreeAsync(W, ctx->stream);
+  if (cs) {
+    // join: the ctx stream (and so the staging free and the caller) follow the last copy
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(done, cs);
+      cudaStreamWaitEvent(st0, done, 0);
+      cudaEventDestroy(done);
+    } else {
+      cudaStreamSynchronize(cs);
+    }
+    cudaStreamDestroy(cs);
+  }
+  for (int q = 0; q < 2; ++q) {
+    if (ev_fill[q]) cudaEventDestroy(ev_fill[q]);
+    if (ev_copy[q]) cudaEventDestroy(ev_copy[q]);
+  }
+  if (stage) cudaFreeAsync(stage, st0);
+  cudaFreeAsync(W, st0);
   return st;
+}
+
+static bie_status check_near_args(const char* who, bie_ctx ctx, bie_surface s, unsigned kernels, double k,
+                                  const void* out) {
+  if (!ctx || !s || !out) { set_error("%s: NULL argument", who); return BIE_EINVAL; }
+  if (!(k > 0) || !(k < 1e6)) { set_error("%s: k must be in (0, 1e6)", who); return BIE_EINVAL; }
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
+    set_error("%s: bad kernel mask %u", who, kernels);
+    return BIE_EINVAL;
+  }
+  return BIE_OK;
 }
 
 bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re, double ws_im,
                              double wk_re, double wk_im, double* A_out) {
-  return assemble_near_impl(ctx, s, kernels, k, ws_re, ws_im, wk_re, wk_im, A_out, false);
+  const bie_status st = check_near_args("bie_assemble_near", ctx, s, kernels, k, A_out);
+  if (st != BIE_OK) return st;
+  const NearOut o = {(cplx*)A_out, s->N, 0, 0};
+  return near_stage(ctx, s, kernels, k, C(ws_re, ws_im), C(wk_re, wk_im), nullptr, o, nullptr);
+}
+
+bie_status bie_assemble_near_band(bie_ctx ctx, bie_surface s, unsigned kernels, double k, double ws_re,
+                                  double ws_im, double wk_re, double wk_im, double* band_out) {
+  const bie_status st = check_near_args("bie_assemble_near_band", ctx, s, kernels, k, band_out);
+  if (st != BIE_OK) return st;
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, band_out);
+  if (e != cudaSuccess) return cuda_fail(e, "bie_assemble_near_band: cudaPointerGetAttributes(band_out)");
+  const NearOut o = {(cplx*)band_out, (int64_t)3 * 16 * s->Mt, 0, 1};
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+    return near_stage(ctx, s, kernels, k, C(ws_re, ws_im), C(wk_re, wk_im), nullptr, o, nullptr);
+  if (at.type == cudaMemoryTypeHost)
+    return near_stage(ctx, s, kernels, k, C(ws_re, ws_im), C(wk_re, wk_im), nullptr, o, (cplx*)band_out);
+  set_error("bie_assemble_near_band: band_out is pageable host memory; give device memory or page-locked "
+            "host memory (cudaHostAlloc / cudaHostRegister)");
+  return BIE_EINVAL;
 }
 
 bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, double eta, double* A_out) {
@@ -232,7 +328,8 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   unsigned kernels = 0;
   if (ws.re != 0.0 || ws.im != 0.0) kernels |= BIE_KERNEL_S;
   if (wk.re != 0.0 || wk.im != 0.0) kernels |= BIE_KERNEL_K;
-  return assemble_near_impl(ctx, s, kernels, k, ws.re, ws.im, wk.re, wk.im, A_out, unweighted);
+  const NearOut o = {(cplx*)A_out, s->N, 0, 0};
+  return near_stage(ctx, s, kernels, k, ws, wk, unweighted ? s->jac : nullptr, o, nullptr);
 }
 
 }  // extern "C"
