@@ -37,8 +37,8 @@ FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (pr
 # modes plus the per-pair records between the two), from one ncu capture of 75,776 pairs of this
 # workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md); valid only for the kernel sources it was
 # taken on: the report carries it while the sources hash to the same value, and null otherwise.
-PAIR_TRAFFIC = {"bytes_per_pair": (11.171584e6 + 296.974080e6 + 245.893632e6 + 123.251200e6) / 75776,
-                "sources": "bd31a062f1086f98"}
+PAIR_TRAFFIC = {"bytes_per_pair": (10.782976e6 + 296.570624e6 + 246.056192e6 + 123.324416e6) / 75776,
+                "sources": "8ca135997c44e2ff"}
 
 
 def algorithmic_flops_per_pair(Mt):

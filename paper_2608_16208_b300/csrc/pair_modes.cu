@@ -319,40 +319,44 @@ __device__ inline double sin_k_minus(int k, double x) {
 }
 
 struct Smem {
-  double *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal, *VK, *VH, *Atab, *Dtab, *Btab;
+  double *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal;
   cplx *W0, *W1, *ph, *kc, *kk;
 };
 
+// Per-warp shared memory of the pair pipeline, in doubles.  Single layer: sn, A~, the two
+// transform buffers, the phases.  With the double layer also tau_0, beta, H3, alpha on the grid,
+// B~, and one buffer of singular modes (kc for S, then kk for K: the S outputs leave first).
 __host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK) {
+  (void)L;
   const int M = Mt / 2;
   size_t d = 0;
   d += Mt;                                   // sn
   d += withK ? 4 * Mt : 0;                   // tau0, bt0, hr, alph
   d += P;                                    // Acal
-  d += withK ? 3 * P : 0;                    // Bcal, VK, VH
-  d += withK ? 3 * (L + 1) : 0;              // Atab, Dtab, Btab
+  d += withK ? P : 0;                        // Bcal
   d += d & 1;                                // W0, W1 start on 16 bytes: the transforms read float4
   d += 4 * P;                                // W0, W1 (complex)
-  d += withK ? 2 * 3 * (2 * M + 1) : 2 * (2 * M + 1);   // ph (, kc, kk)
+  d += withK ? 2 * 2 * (2 * M + 1) : 2 * (2 * M + 1);   // ph (, kc = kk)
   return d;
 }
 
 __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
+  (void)L;
   const int M = Mt / 2;
   Smem s = {};
   double* p = base;
   s.sn = p; p += Mt;
   if (withK) { s.tau0 = p; p += Mt; s.bt0 = p; p += Mt; s.hr = p; p += Mt; s.alph = p; p += Mt; }
   s.Acal = p; p += P;
-  if (withK) { s.Bcal = p; p += P; s.VK = p; p += P; s.VH = p; p += P; }
-  if (withK) { s.Atab = p; p += L + 1; s.Dtab = p; p += L + 1; s.Btab = p; p += L + 1; }
+  if (withK) { s.Bcal = p; p += P; }
   p += (p - base) & 1;   // 16-byte start for the double-word transforms
   s.W0 = (cplx*)p; p += 2 * P;
   s.W1 = (cplx*)p; p += 2 * P;
   s.ph = (cplx*)p; p += 2 * (2 * M + 1);
   if (withK) {
-    s.kc = (cplx*)p; p += 2 * (2 * M + 1);
-    s.kk = (cplx*)p; p += 2 * (2 * M + 1);
+    s.kc = (cplx*)p;
+    s.kk = s.kc;
+    p += 2 * (2 * M + 1);
   }
   return s;
 }
@@ -717,7 +721,42 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
     // upsampling, the S product, the outputs) run in double words; those of the double layer stay
     // FP64: they pack signals of very different size (tau_0 ~ curvature rho^2 beside alpha ~ k^2,
     // A beside B, V_K A~ beside V_H), and extracting the small one costs digits in proportion.
-    int acal_next = -1;   // pair whose circulant transform already sits in Acal (single layer alone)
+    // Shared memory per warp holds only what outlives a step: A~ and B~ are rescaled in place
+    // (A~ -> F~ A~ -> alpha~ tau0~ F~ A~, B~ -> h3~ B~), A_m, D_m and B_m are read from the
+    // batch's recurrence scratch, and the single-layer outputs leave before the double layer's
+    // singular modes take their buffer.
+    auto emit = [&](int64_t p, int kidx, bool isS, const cplx* sing) {
+      if (a.modes_out) {
+        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(isS ? sm.sn[q] : sm.bt0[q], 0.0);
+        __syncwarp();
+        const cplx* Sf = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
+        double* out = a.modes_out + (p * nk + kidx) * 2 * (Mt + 1);
+        for (int mm = lane; mm <= 2 * M; mm += 32) {
+          const int m = mm - M;
+          cplx sv = Sf[wrapi(m, Mt)] * (1.0 / Mt);
+          if (m == M || m == -M) sv = 0.5 * sv;
+          const cplx smooth = isS ? C(-sv.im, sv.re) : C(sv.im, -sv.re);   // i <sn> or -i <beta tau0>
+          out[2 * mm] = sing[mm].re + smooth.re;
+          out[2 * mm + 1] = sing[mm].im + smooth.im;
+        }
+        __syncwarp();
+      }
+      if (a.weights_out) {
+        for (int q = lane; q < Mt; q += 32) {
+          const int m = q < M ? q : q - Mt;
+          sm.W0[q] = (q == M) ? 0.5 * (sing[2 * M] + sing[0]) : sing[m + M];
+        }
+        __syncwarp();
+        const cplx* Wt = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, +1);
+        cplx* wout = a.weights_out + kidx * a.weights_stride + p * a.w_ld;
+        for (int q = lane; q < Mt; q += 32) {
+          const cplx w = Wt[q] * (1.0 / Mt);
+          const double sv = (isS ? sm.sn[q] : -sm.bt0[q]) / Mt;
+          wout[q] = C(w.re, w.im + sv);
+        }
+        __syncwarp();
+      }
+    };
     for (int pi = 0; pi < nb; ++pi) {
       const PairInfo pr = bcast(mine, pi);
       const int64_t p = a.out_mod ? (a.out_base + p0 + pi) % a.out_mod : p0 + pi;   // output slot
@@ -734,48 +773,23 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       const double* rn = a.ring_n + pr.ring * 3 * Mt;
       const double dts = fabs(pr.t - pr.ts);
       const double qb = exp(-rb), om = -expm1(-rb);
-      const bool translated = wantK && rb < kSmallB;
-      // ---- D1. A_m (and D_m, B_m) of this pair; phases e^{ija}
-      if (wantK)
-        for (int m = lane; m <= L; m += 32) {
-          sm.Atab[m] = scrA[m * 32 + pi];
-          sm.Dtab[m] = scrD[m * 32 + pi];
-        }
-      if (wantK) {
-        // e^{ija}, j = -M..M, each from its own sincos: the translated tau_3 combines phase-weighted
-        // terms that cancel, so a rotation recurrence's ulp drift would be amplified
-        for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
-      } else {
-        // single layer: e^{ija} for j = lane + 32k by steps of e^{32ia} (a few ulp), e^{-ija} = conj
-        cplx e = cexpi(lane * ra);
-        const cplx step = cexpi(32.0 * ra);
-        for (int j = lane; j <= M; j += 32) {
-          sm.ph[M + j] = e;
-          sm.ph[M - j] = conj(e);
-          e = e * step;
-        }
-      }
-      __syncwarp();
-      if (wantK) {  // B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b, m = 0..2M+1
-        const double shb = sinh(rb), sh2b = sinh(0.5 * rb) * sinh(0.5 * rb);
-        const double fac = exp(rb) / (shb * shb);
-        for (int m = lane; m <= 2 * M + 1; m += 32)
-          sm.Btab[m] = -(m - 0.5) * fac * (sm.Dtab[m] + 2 * sh2b * sm.Atab[m]);
-        __syncwarp();
-      }
-      // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and, with K, B_{|d|} or B~_{|d|} (|d| <= 2M).
-      // Single layer alone: the transform of this pair's circulant usually arrived packed with the
-      // previous pair's Toeplitz transform (acal_next); compute it here only when it did not.
-      if (!wantK && acal_next == pi) {
-        // already in Acal
-      } else {
+      const bool translated = rb < kSmallB;
+      // ---- D1. phases e^{ija}, each from its own sincos: the translated tau_3 combines
+      // phase-weighted terms that cancel, so a rotation recurrence's ulp drift would be amplified
+      for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
+      // A_m and B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b from the scratch
+      const double shb = sinh(rb), sh2b = sinh(0.5 * rb) * sinh(0.5 * rb);
+      const double fac = exp(rb) / (shb * shb);
+      auto Am = [&](int m) { return scrA[m * 32 + pi]; };
+      auto Bm = [&](int m) { return -(m - 0.5) * fac * (scrD[m * 32 + pi] + 2 * sh2b * scrA[m * 32 + pi]); };
+      // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and B_{|d|} or B~_{|d|} (|d| <= 2M)
       for (int pp = lane; pp < P; pp += 32) {
         const int dd = pp <= P / 2 ? pp : P - pp;
-        const double av = dd <= L ? scrA[dd * 32 + pi] : 0.0;
+        const double av = dd <= L ? Am(dd) : 0.0;
         double bv = 0.0;
-        if (wantK && dd <= 2 * M) {
-          bv = sm.Btab[dd];
-          if (translated) bv = (sm.Atab[dd] - om * om * bv) / (4 * qb);
+        if (dd <= 2 * M) {
+          bv = Bm(dd);
+          if (translated) bv = (Am(dd) - om * om * bv) / (4 * qb);
         }
         sm.W1[pp] = C(av, bv);
       }
@@ -784,11 +798,10 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         const cplx* Af = warp_fft(sm.W1, sm.W0, P, a.tw, a.T, -1);
         for (int pp = lane; pp < P; pp += 32) {
           sm.Acal[pp] = Af[pp].re;
-          if (wantK) sm.Bcal[pp] = Af[pp].im;
+          sm.Bcal[pp] = Af[pp].im;
         }
       }
       __syncwarp();
-      }
       // ---- D3. samples
       double sha, cha;   // sin(a/2), cos(a/2)
       sincos(0.5 * ra, &sha, &cha);
@@ -815,34 +828,32 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         sincos(a.k * rho, &skr, &ckr);
         sm.W0[q] = C(F, ckr);          // F + i cos(k rho)
         sm.sn[q] = skr * rinv;
-        if (wantK) {
-          const double x = a.k * rho;
-          double al, be;
-          if (x < kSeriesX) {  // Taylor series of alpha/k^2 and beta/k^3
-            const double x2 = x * x;
-            double sa = 0.0, sb = 0.0, pw = 1.0, fa = 2.0, fb = 6.0;
-            for (int n = 1; n <= 9; ++n) {
-              const double sg = (n & 1) ? 1.0 : -1.0;
-              sa += sg * (1 - 2 * n) / fa * pw;
-              sb += sg * (2 * n) / fb * pw;
-              pw *= x2;
-              fa *= (2 * n + 1) * (2 * n + 2);
-              fb *= (2 * n + 2) * (2 * n + 3);
-            }
-            al = a.k * a.k * sa;
-            be = a.k * a.k * a.k * sb;
-          } else {
-            al = (1 - ckr - x * skr) / r2;
-            be = (skr - x * ckr) / (r2 * rho);
+        const double x = a.k * rho;
+        double al, be;
+        if (x < kSeriesX) {  // Taylor series of alpha/k^2 and beta/k^3
+          const double x2 = x * x;
+          double sa = 0.0, sb = 0.0, pw = 1.0, fa = 2.0, fb = 6.0;
+          for (int n = 1; n <= 9; ++n) {
+            const double sg = (n & 1) ? 1.0 : -1.0;
+            sa += sg * (1 - 2 * n) / fa * pw;
+            sb += sg * (2 * n) / fb * pw;
+            pw *= x2;
+            fa *= (2 * n + 1) * (2 * n + 2);
+            fb *= (2 * n + 2) * (2 * n + 3);
           }
-          sm.tau0[q] = rn[3 * q] * yx + rn[3 * q + 1] * yy + rn[3 * q + 2] * yz;   // near ones replaced below
-          sm.alph[q] = al;
-          sm.bt0[q] = be;
-          sm.hr[q] = F;
+          al = a.k * a.k * sa;
+          be = a.k * a.k * a.k * sb;
+        } else {
+          al = (1 - ckr - x * skr) / r2;
+          be = (skr - x * ckr) / (r2 * rho);
         }
+        sm.tau0[q] = rn[3 * q] * yx + rn[3 * q + 1] * yy + rn[3 * q + 2] * yz;   // near ones replaced below
+        sm.alph[q] = al;
+        sm.bt0[q] = be;
+        sm.hr[q] = F;
       }
       __syncwarp();
-      if (wantK) {
+      {
         // tau_0 of near samples: second-derivative line integral (Section 4 Remark), 16 lanes per sample
         const int i = (int)(pr.row % Mt);
         const int Kw = (int)ceil(kStableDelta * Mt / kTwoPi) + 1;
@@ -876,7 +887,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         }
         __syncwarp();
       }
-      // ---- D4. S: FFT of F + i cos(k rho), upsample, Toeplitz with A
+      // ---- D4. FFT of F + i cos(k rho), upsample; A~ <- F~ A~; S: Toeplitz with A, then its outputs
       cplx* Z1 = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
       cplx* Zf = (Z1 == sm.W0) ? sm.W1 : sm.W0;
       double dFa = 0.0;   // F'(a) from the interpolant of F (well conditioned, unlike the direct form)
@@ -894,207 +905,148 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       }
       cplx* up1 = upsample(Z1, sm.ph, Zf, Z1, Mt, P, a.tw, a.twf, a.T, true);   // re: F~, im: C~
       cplx* uf = (up1 == sm.W0) ? sm.W1 : sm.W0;
-      if (wantK)
-        for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up1[pp].re;   // keep F~ for V_K
-      if (wantS && !wantK) {
-        // U = F~ C~ Acal (real) in the real part; the next valid pair's circulant A_{|d|} (real, even)
-        // in the imaginary part: one transform serves both
-        const unsigned later = valid_mask & ~((2u << pi) - 1u);   // valid pairs after pi
-        const int nxt = later ? __ffs(later) - 1 : nb;
-        const bool pack = nxt < nb;
-        for (int pp = lane; pp < P; pp += 32) {
-          const int dd = pp <= P / 2 ? pp : P - pp;
-          const double an = (pack && dd <= L) ? scrA[dd * 32 + nxt] : 0.0;
-          uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], an);
-        }
-        __syncwarp();
-        const cplx* Yf = warp_fft_x(uf, up1, P, a.twf, a.T, -1);
-        for (int jj = lane; jj <= 2 * M; jj += 32) {
-          const int m = jj - M;
-          const cplx zp = Yf[wrapi(m, P)], zm = conj(Yf[wrapi(-m, P)]);
-          sm.kc[jj] = conj(sm.ph[jj]) * (0.5 * (zp + zm)) * (1.0 / P);
-        }
-        if (pack) {
-          __syncwarp();
-          // transform of the (real, even) circulant = (Z_p - conj Z_{-p}) / (2i), real
-          for (int pp = lane; pp < P; pp += 32) {
-            const cplx zp = Yf[pp], zm = conj(Yf[(P - pp) % P]);
-            sm.Acal[pp] = 0.5 * (zp.im - zm.im);
-          }
-          acal_next = nxt;
-        }
-      } else if (wantS) {
-        for (int pp = lane; pp < P; pp += 32) uf[pp] = C(up1[pp].re * up1[pp].im * sm.Acal[pp], 0.0);
-        __syncwarp();
-        const cplx* Yf = warp_fft_x(uf, up1, P, a.twf, a.T, -1);
-        for (int jj = lane; jj <= 2 * M; jj += 32) sm.kc[jj] = conj(sm.ph[jj]) * Yf[wrapi(jj - M, P)] * (1.0 / P);
+      for (int pp = lane; pp < P; pp += 32) {
+        const double g = up1[pp].re * sm.Acal[pp];   // F~ A~ (kept for V_K)
+        sm.Acal[pp] = g;
+        if (wantS) uf[pp] = C(up1[pp].im * g, 0.0);
       }
       __syncwarp();
-      if (wantK) {
-        // ---- D5. V_K = alpha~ tau0~ F~ on the P grid
-        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], sm.alph[q]);
+      if (wantS) {
+        const cplx* Yf = warp_fft_x(uf, up1, P, a.twf, a.T, -1);
+        for (int jj = lane; jj <= 2 * M; jj += 32) sm.kc[jj] = conj(sm.ph[jj]) * Yf[wrapi(jj - M, P)] * (1.0 / P);
         __syncwarp();
-        cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
-        cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
-        cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.twf, a.T, false);   // re: tau0~, im: alpha~
-        for (int pp = lane; pp < P; pp += 32) sm.VK[pp] = up2[pp].re * up2[pp].im * sm.VH[pp];
+        emit(p, 0, true, sm.kc);
+      }
+      // ---- D5. A~ <- V_K A~ = alpha~ tau0~ F~ A~ on the P grid
+      for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], sm.alph[q]);
+      __syncwarp();
+      cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+      cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
+      cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.twf, a.T, false);   // re: tau0~, im: alpha~
+      for (int pp = lane; pp < P; pp += 32) sm.Acal[pp] = up2[pp].re * up2[pp].im * sm.Acal[pp];
+      __syncwarp();
+      // ---- D6. H3 modes (symmetric), with beta tau_0 packed in the imaginary part (kk: kc is spent)
+      for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.hr[q], sm.bt0[q]);
+      __syncwarp();
+      const cplx* Z3 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+      for (int jj = lane; jj <= 2 * M; jj += 32) {
+        const int jv = jj - M;
+        const cplx zp = Z3[wrapi(jv, Mt)], zm = conj(Z3[wrapi(-jv, Mt)]);
+        cplx h = 0.5 * (zp + zm) * (1.0 / Mt);
+        if (jv == M || jv == -M) h = 0.5 * h;
+        sm.kk[jj] = h;
+      }
+      __syncwarp();
+      double H3a = 0.0, H3pa = 0.0;
+      if (translated) {
+        // ---- D7. H3(a), H3'(a) directly from the geometry at th_s = a
+        const bool neara = dts + fabs(wrap_pi(ra - pr.th)) <= kStableDelta;
+        R3 Y;
+        Geo G;
+        surf_eval(a.S, pr.ts, ra, 2, &G);
+        if (neara) Y = diff_ana<double>(a.S, pr.ts, ra, pr.t, pr.th);
+        else Y = {G.r.x - pr.x, G.r.y - pr.y, G.r.z - pr.z};
+        const R3 n = cross(G.rt, G.rth);
+        const double J = sqrt(dot(n, n));
+        const R3 nu = {n.x / J, n.y / J, n.z / J};
+        const R3 dn1 = cross(G.rtth, G.rth), dn2 = cross(G.rt, G.rthth);
+        const R3 dn = {dn1.x + dn2.x, dn1.y + dn2.y, dn1.z + dn2.z};
+        const double nd = dot(nu, dn);
+        const R3 dnu = {(dn.x - nu.x * nd) / J, (dn.y - nu.y * nd) / J, (dn.z - nu.z * nd) / J};
+        double t0a = dot(nu, Y);
+        if (neara) {
+          double acc = 0.0;
+          if (lane < 16) {
+            const double dt = pr.t - pr.ts, dth = wrap_pi(pr.th - ra), lam = a.gl.x[lane];
+            Geo H;
+            surf_eval(a.S, pr.ts + lam * dt, ra + lam * dth, 2, &H);
+            const double qx = H.rtt.x * dt * dt + 2 * H.rtth.x * dt * dth + H.rthth.x * dth * dth;
+            const double qy = H.rtt.y * dt * dt + 2 * H.rtth.y * dt * dth + H.rthth.y * dth * dth;
+            const double qz = H.rtt.z * dt * dt + 2 * H.rtth.z * dt * dth + H.rthth.z * dth * dth;
+            acc = a.gl.w[lane] * (lam - 1) * (nu.x * qx + nu.y * qy + nu.z * qz);
+          }
+          t0a = warp_sum(acc);
+        }
+        const double r2a = dot(Y, Y);
+        const double Fa = om / sqrt(r2a);
+        const double dt0 = dot(dnu, Y);
+        H3a = t0a * Fa * Fa * Fa;
+        H3pa = dt0 * Fa * Fa * Fa + 3 * t0a * Fa * Fa * dFa;
+        // ---- D8. remainder R on the grid (stable sum within kNearPhi of a); modes d_k
+        for (int q = lane; q < Mt; q += 32) {
+          const double phq = wrap_pi(kTwoPi * q / Mt - ra);
+          const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
+          sm.tau0[q] = (fabs(phq) < kNearPhi) ? 0.0 : (sm.hr[q] - H3a - H3pa * sin(phq)) / s2;
+        }
         __syncwarp();
-        // ---- D6. H3 modes (symmetric), with beta tau_0 packed in the imaginary part
-        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.hr[q], sm.bt0[q]);
+        for (int q = 0; q < Mt; ++q) {
+          const double phq = wrap_pi(kTwoPi * q / Mt - ra);
+          if (!(fabs(phq) < kNearPhi)) continue;
+          const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
+          double acc = 0.0;
+          for (int jj = lane; jj <= 2 * M; jj += 32) {
+            const int kv = jj - M, ka = kv < 0 ? -kv : kv;
+            const cplx hv = sm.kk[jj] * sm.ph[jj];   // h3_k e^{ika}
+            double gre, gim;
+            if (s2 == 0.0) {
+              gre = -2.0 * ka * ka;
+              gim = 0.0;
+            } else {
+              const double sk = sin(0.5 * ka * phq);
+              gre = -2.0 * sk * sk / s2;
+              gim = (kv < 0 ? -1.0 : 1.0) * sin_k_minus(ka, phq) / s2;
+            }
+            acc += hv.re * gre - hv.im * gim;
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) sm.tau0[q] = acc;
+          __syncwarp();
+        }
         __syncwarp();
-        const cplx* Z3 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], 0.0);
+        __syncwarp();
+        const cplx* Zr = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
         for (int jj = lane; jj <= 2 * M; jj += 32) {
           const int jv = jj - M;
-          const cplx zp = Z3[wrapi(jv, Mt)], zm = conj(Z3[wrapi(-jv, Mt)]);
-          cplx h = 0.5 * (zp + zm) * (1.0 / Mt);
-          if (jv == M || jv == -M) h = 0.5 * h;
-          sm.kk[jj] = h;
+          cplx dv = Zr[wrapi(jv, Mt)] * (1.0 / Mt);
+          if (jv == M || jv == -M) dv = 0.5 * dv;
+          sm.kk[jj] = dv;        // kk now holds d_k
         }
         __syncwarp();
-        double H3a = 0.0, H3pa = 0.0;
+      }
+      // ---- D9. upsample h3 (or d); B~ <- V_H = h3~ B~
+      {
+        for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(0.0);
+        __syncwarp();
+        for (int jj = lane; jj <= 2 * M; jj += 32) sm.W0[wrapi(jj - M, P)] = sm.ph[jj] * sm.kk[jj];
+        __syncwarp();
+        const cplx* up3 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, +1);
+        for (int pp = lane; pp < P; pp += 32) sm.Bcal[pp] = up3[pp].re * sm.Bcal[pp];
+        __syncwarp();
+      }
+      // ---- D10. transform (V_K A~) + i (V_H), unpack AT1 and the tau_3 Toeplitz part
+      for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(sm.Acal[pp], sm.Bcal[pp]);
+      __syncwarp();
+      const cplx* Y2 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, -1);
+      for (int jj = lane; jj <= 2 * M; jj += 32) {
+        const int m = jj - M;
+        const cplx zp = Y2[wrapi(m, P)], zm = conj(Y2[wrapi(-m, P)]);
+        const cplx y1 = 0.5 * (zp + zm) * (1.0 / P);
+        const cplx y2 = C(0.5 * (zp.im - zm.im), -0.5 * (zp.re - zm.re)) * (1.0 / P);
+        const cplx e = conj(sm.ph[jj]);                                  // e^{-ima}
+        cplx t3 = e * y2;
         if (translated) {
-          // ---- D7. H3(a), H3'(a) directly from the geometry at th_s = a
-          const bool neara = dts + fabs(wrap_pi(ra - pr.th)) <= kStableDelta;
-          R3 Y;
-          Geo G;
-          surf_eval(a.S, pr.ts, ra, 2, &G);
-          if (neara) Y = diff_ana<double>(a.S, pr.ts, ra, pr.t, pr.th);
-          else Y = {G.r.x - pr.x, G.r.y - pr.y, G.r.z - pr.z};
-          const R3 n = cross(G.rt, G.rth);
-          const double J = sqrt(dot(n, n));
-          const R3 nu = {n.x / J, n.y / J, n.z / J};
-          const R3 dn1 = cross(G.rtth, G.rth), dn2 = cross(G.rt, G.rthth);
-          const R3 dn = {dn1.x + dn2.x, dn1.y + dn2.y, dn1.z + dn2.z};
-          const double nd = dot(nu, dn);
-          const R3 dnu = {(dn.x - nu.x * nd) / J, (dn.y - nu.y * nd) / J, (dn.z - nu.z * nd) / J};
-          double t0a = dot(nu, Y);
-          if (neara) {
-            double acc = 0.0;
-            if (lane < 16) {
-              const double dt = pr.t - pr.ts, dth = wrap_pi(pr.th - ra), lam = a.gl.x[lane];
-              Geo H;
-              surf_eval(a.S, pr.ts + lam * dt, ra + lam * dth, 2, &H);
-              const double qx = H.rtt.x * dt * dt + 2 * H.rtth.x * dt * dth + H.rthth.x * dth * dth;
-              const double qy = H.rtt.y * dt * dt + 2 * H.rtth.y * dt * dth + H.rthth.y * dth * dth;
-              const double qz = H.rtt.z * dt * dt + 2 * H.rtth.z * dt * dth + H.rthth.z * dth * dth;
-              acc = a.gl.w[lane] * (lam - 1) * (nu.x * qx + nu.y * qy + nu.z * qz);
-            }
-            t0a = warp_sum(acc);
-          }
-          const double r2a = dot(Y, Y);
-          const double Fa = om / sqrt(r2a);
-          const double dt0 = dot(dnu, Y);
-          H3a = t0a * Fa * Fa * Fa;
-          H3pa = dt0 * Fa * Fa * Fa + 3 * t0a * Fa * Fa * dFa;
-          // ---- D8. remainder R on the grid (stable sum within kNearPhi of a); modes d_k
-          for (int q = lane; q < Mt; q += 32) {
-            const double phq = wrap_pi(kTwoPi * q / Mt - ra);
-            const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
-            sm.tau0[q] = (fabs(phq) < kNearPhi) ? 0.0 : (sm.hr[q] - H3a - H3pa * sin(phq)) / s2;
-          }
-          __syncwarp();
-          for (int q = 0; q < Mt; ++q) {
-            const double phq = wrap_pi(kTwoPi * q / Mt - ra);
-            if (!(fabs(phq) < kNearPhi)) continue;
-            const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
-            double acc = 0.0;
-            for (int jj = lane; jj <= 2 * M; jj += 32) {
-              const int kv = jj - M, ka = kv < 0 ? -kv : kv;
-              const cplx hv = sm.kk[jj] * sm.ph[jj];   // h3_k e^{ika}
-              double gre, gim;
-              if (s2 == 0.0) {
-                gre = -2.0 * ka * ka;
-                gim = 0.0;
-              } else {
-                const double sk = sin(0.5 * ka * phq);
-                gre = -2.0 * sk * sk / s2;
-                gim = (kv < 0 ? -1.0 : 1.0) * sin_k_minus(ka, phq) / s2;
-              }
-              acc += hv.re * gre - hv.im * gim;
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) sm.tau0[q] = acc;
-            __syncwarp();
-          }
-          __syncwarp();
-          for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], 0.0);
-          __syncwarp();
-          const cplx* Zr = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
-          for (int jj = lane; jj <= 2 * M; jj += 32) {
-            const int jv = jj - M;
-            cplx dv = Zr[wrapi(jv, Mt)] * (1.0 / Mt);
-            if (jv == M || jv == -M) dv = 0.5 * dv;
-            sm.kk[jj] = dv;        // kk now holds d_k
-          }
-          __syncwarp();
+          // H3(a) B_n(a,b) + H3'(a)/(2i) e^{-ina} (B_{|n-1|} - B_{|n+1|}), with the exact
+          // cancellation-free B_{n-1} - B_{n+1} = 2 n e^b A_{|n|}
+          const int ma = m < 0 ? -m : m;
+          const cplx expl = C(H3a * Bm(ma), -H3pa * m * exp(rb) * Am(ma));
+          t3 = t3 + e * expl;
         }
-        // ---- D9. upsample h3 (or d), multiply by the B (or B~) transform
-        {
-          for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(0.0);
-          __syncwarp();
-          for (int jj = lane; jj <= 2 * M; jj += 32) sm.W0[wrapi(jj - M, P)] = sm.ph[jj] * sm.kk[jj];
-          __syncwarp();
-          const cplx* up3 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, +1);
-          for (int pp = lane; pp < P; pp += 32) sm.VH[pp] = up3[pp].re * sm.Bcal[pp];
-          __syncwarp();
-        }
-        // ---- D10. transform (V_K Acal) + i (V_H), unpack AT1 and the tau_3 Toeplitz part
-        for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(sm.VK[pp] * sm.Acal[pp], sm.VH[pp]);
-        __syncwarp();
-        const cplx* Y2 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, -1);
-        for (int jj = lane; jj <= 2 * M; jj += 32) {
-          const int m = jj - M;
-          const cplx zp = Y2[wrapi(m, P)], zm = conj(Y2[wrapi(-m, P)]);
-          const cplx y1 = 0.5 * (zp + zm) * (1.0 / P);
-          const cplx y2 = C(0.5 * (zp.im - zm.im), -0.5 * (zp.re - zm.re)) * (1.0 / P);
-          const cplx e = conj(sm.ph[jj]);                                  // e^{-ima}
-          cplx t3 = e * y2;
-          if (translated) {
-            // H3(a) B_n(a,b) + H3'(a)/(2i) e^{-ina} (B_{|n-1|} - B_{|n+1|}), with the exact
-            // cancellation-free B_{n-1} - B_{n+1} = 2 n e^b A_{|n|}
-            const int ma = m < 0 ? -m : m;
-            const cplx expl = C(H3a * sm.Btab[ma], -H3pa * m * exp(rb) * sm.Atab[ma]);
-            t3 = t3 + e * expl;
-          }
-          sm.kk[jj] = e * y1 - t3;   // swapped part of K (kk was consumed in D9)
-        }
-        __syncwarp();
+        sm.kk[jj] = e * y1 - t3;   // swapped part of K (kk was consumed in D9)
       }
-      // ---- D11. outputs
-      for (int kidx = 0; kidx < nk; ++kidx) {
-        const bool isS = wantS && kidx == 0;
-        const cplx* sing = isS ? sm.kc : sm.kk;
-        if (a.modes_out) {
-          for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(isS ? sm.sn[q] : sm.bt0[q], 0.0);
-          __syncwarp();
-          const cplx* Sf = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
-          double* out = a.modes_out + (p * nk + kidx) * 2 * (Mt + 1);
-          for (int mm = lane; mm <= 2 * M; mm += 32) {
-            const int m = mm - M;
-            cplx sv = Sf[wrapi(m, Mt)] * (1.0 / Mt);
-            if (m == M || m == -M) sv = 0.5 * sv;
-            const cplx smooth = isS ? C(-sv.im, sv.re) : C(sv.im, -sv.re);   // i <sn> or -i <beta tau0>
-            out[2 * mm] = sing[mm].re + smooth.re;
-            out[2 * mm + 1] = sing[mm].im + smooth.im;
-          }
-          __syncwarp();
-        }
-        if (a.weights_out) {
-          for (int q = lane; q < Mt; q += 32) {
-            const int m = q < M ? q : q - Mt;
-            sm.W0[q] = (q == M) ? 0.5 * (sing[2 * M] + sing[0]) : sing[m + M];
-          }
-          __syncwarp();
-          const cplx* Wt = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, +1);
-          cplx* wout = a.weights_out + kidx * a.weights_stride + p * a.w_ld;
-          for (int q = lane; q < Mt; q += 32) {
-            const cplx w = Wt[q] * (1.0 / Mt);
-            const double sv = (isS ? sm.sn[q] : -sm.bt0[q]) / Mt;
-            wout[q] = C(w.re, w.im + sv);
-          }
-          __syncwarp();
-        }
-      }
+      __syncwarp();
+      // ---- D11. double-layer outputs
+      emit(p, nk - 1, false, sm.kk);
     }
     }
     __syncwarp();
