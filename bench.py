@@ -32,6 +32,16 @@ import workloads as wl  # noqa: E402
 WORKLOAD = "ellipsoid_np16_m128_k10"
 METRIC = "kernel-mode pairs/s (correction stage, S kernel, FP64)"
 UNIT = "pairs/s"
+def _hbm_peak():
+    """Measured copy bandwidth of the B300s (GB/s) and its source."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
 FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (profiles/fp64_peak_probe.md)
 # DRAM bytes (read + write) per pair of the pair pipeline (root kernel + transform kernel: the kernel
 # modes plus the per-pair records between the two), from one ncu capture of 75,776 pairs of this
@@ -311,6 +321,8 @@ def run_gpu(args):
         res["learned"] = run_learned(bie) if args.learned else None
         solve = res
 
+    rows = run_rows(bie, surf, k, A, flush, stream, step_ms, solve)
+
     batch = None if args.batch_surfaces <= 0 else run_batch(bie, ctx, args.batch_surfaces, stream)
 
     if rank == 0:
@@ -335,6 +347,7 @@ def run_gpu(args):
                              "sample": "%d near pairs of 400 seeded target rows, method mode, %.1f s" % (cpu_n, cpu_dt)},
             "solve": solve,
             "batch": batch,
+            "rows": rows,
             "single_and_double_layer": {"pairs_per_s": pk_pairs / (sk_ms / 1000.0), "ms": sk_ms, "pairs": pk_pairs,
                                         "kernels": "S+K", "path": "fused FP64 pair kernel"},
         }
@@ -461,6 +474,55 @@ def run_learned(bie, n_train=4, n_test=2, steps=600):
             "train_systems": n_train, "train_steps": steps, "batch": 16, "train_seconds": t_train,
             "loss_first10": float(np.mean(hist[:10])), "loss_last50": float(np.mean(hist[-50:])),
             "blockdiag_factor_seconds": float(np.median(lu_times)), "held_out": held}
+
+
+def run_rows(bie, surf, k, A, flush, stream, near_ms, solve):
+    """Figures of the steps around the pair pipeline on the same surface: the far fill (whole S
+    assembly minus the correction stage), the FGMRES matvec (per iteration of the solves above) and
+    the field evaluation at exterior points."""
+    import torch
+    N = surf.N
+    hbm, hbm_src = _hbm_peak()
+
+    def timed(fn, reps=3):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
+    rows = {}
+    asm_ms = timed(lambda: bie.assemble(surf, bie.OP_S, k, out=A))
+    far_ms = asm_ms - near_ms
+    rows["far_fill"] = {
+        "assemble_ms": asm_ms, "correction_ms": near_ms, "far_fill_ms": far_ms,
+        "entries_per_s": N * N / (far_ms / 1000.0),
+        "write_GBps": 16.0 * N * N / (far_ms / 1000.0) / 1e9, "hbm_peak_GBps": hbm, "hbm_peak_source": hbm_src,
+        "frac_of_hbm": 16.0 * N * N / (far_ms / 1000.0) / 1e9 / hbm,
+        "bound": "FP64: one rsqrt and one sincos per entry (writes 16 B per entry)"}
+    if solve is not None:
+        mv = {}
+        for name, bytes_per in (("fp64", 16), ("mixed_fp32_refined", 8)):
+            rep = solve.get(name, {})
+            if rep.get("iterations"):
+                per = 1000.0 * rep["seconds"] / rep["iterations"]
+                mv[name] = {"ms_per_iteration": per, "matrix_bytes": bytes_per * N * N,
+                            "implied_read_GBps": bytes_per * N * N / (per / 1000.0) / 1e9}
+        mv["note"] = ("iteration time covers the matvec, the Arnoldi step and, for the mixed solve, its "
+                      "share of the FP64 refinement residuals; the implied rate is a lower bound on the matvec's")
+        rows["matvec"] = mv
+    pts = torch.as_tensor(wl.exterior_points(8192, 3.0), dtype=torch.float64).cuda()
+    dens = torch.as_tensor(wl.random_complex((N,), 0, 13), dtype=torch.complex128).cuda()
+    fe_ms = timed(lambda: bie.field_eval(surf, bie.OP_S, k, dens, pts))
+    rows["field_eval"] = {"points": int(pts.shape[0]), "sources": N, "ms": fe_ms,
+                          "source_point_pairs_per_s": N * pts.shape[0] / (fe_ms / 1000.0),
+                          "bound": "FP64: one rsqrt and one sincos per source-point pair"}
+    return rows
 
 
 def run_kernel_only(n):

@@ -29,14 +29,23 @@ struct FarArgs {
   const double* pts;
   const double* nrm;
   const double* jac;
-  double wgl[16];       // Gauss-Legendre weights on [-1, 1]
+  double wq[16];        // (h/2) w_n / Mt: Gauss-Legendre weight on [-1, 1] times the panel and trapezoid factors
   cplx* A;
 };
 
+// k rho below which the entry's phase goes through the double-word sin/cos (FP64 reduction by pi/2)
+constexpr double kFarDwMaxPhase = 4096.0;
+
 // One thread per (row, column); grid-stride over the N x N entries, rows in blockIdx.y chunks.
+// FP64 for the differences, rho^2, rsqrt and k rho (the phase keeps FP64 accuracy); the sin/cos
+// series and the products of the entry in double words, so that the FP64 pipe carries about a third
+// of the instructions of an all-FP64 entry.
 __global__ void far_fill_kernel(const FarArgs a) {
   const int64_t N = a.N;
   const int64_t per_panel = (int64_t)16 * a.Mt;
+  const bool wantS = a.ws.re != 0.0 || a.ws.im != 0.0;
+  const bool wantK = a.wk.re != 0.0 || a.wk.im != 0.0;
+  const float4 wsd = dwc_from(a.ws), wkd = dwc_from(a.wk);
   for (int64_t row = blockIdx.y; row < N; row += gridDim.y) {
     const double xx = a.pts[3 * row], xy = a.pts[3 * row + 1], xz = a.pts[3 * row + 2];
     const int jrow = (int)(row / per_panel);
@@ -49,19 +58,33 @@ __global__ void far_fill_kernel(const FarArgs a) {
         const double r2 = yx * yx + yy * yy + yz * yz;
         const double rinv = rsqrt(r2);
         const double rho = r2 * rinv;
-        double s, c;
-        sincos(a.k * rho, &s, &c);
+        const double x = a.k * rho;
         const int n = (int)((col / a.Mt) % 16);
-        const double w = a.h * 0.5 * a.wgl[n] / a.Mt;
-        cplx e = C(c, s);
-        cplx val = C(0.0);
-        if (a.ws.re != 0.0 || a.ws.im != 0.0) val = rinv * (a.ws * e);
-        if (a.wk.re != 0.0 || a.wk.im != 0.0) {
-          const double tau0 = a.nrm[3 * col] * yx + a.nrm[3 * col + 1] * yy + a.nrm[3 * col + 2] * yz;
-          const double f = tau0 * rinv * rinv * rinv;
-          val = val + f * (a.wk * (e * C(-1.0, a.k * rho)));
+        const double w = a.unweighted ? a.wq[n] * a.jac[col] : a.wq[n];
+        const double tau0 = wantK ? a.nrm[3 * col] * yx + a.nrm[3 * col + 1] * yy + a.nrm[3 * col + 2] * yz : 0.0;
+        if (x < kFarDwMaxPhase) {
+          float2 sn, cs;
+          dw_sincos(x, &sn, &cs);
+          const float2 ri = dw_from(rinv);
+          float4 val = dwc_zero();
+          if (wantS) val = dwc_mul(wsd, mkc(dw_mul(cs, ri), dw_mul(sn, ri)));   // ws e^{ik rho} / rho
+          if (wantK) {
+            // wk tau0 / rho^3 e^{ik rho} (ik rho - 1) = wk tau0 / rho^3 ((-cos - x sin) + i (x cos - sin))
+            const float2 xd = dw_from(x);
+            const float2 f = dw_mul(dw_from(tau0), dw_mul(ri, dw_mul(ri, ri)));
+            const float4 g = mkc(dw_sub(dw_neg(cs), dw_mul(xd, sn)), dw_sub(dw_mul(xd, cs), sn));
+            val = dwc_add(val, dwc_mul(wkd, dwc_mulr(g, f)));
+          }
+          v = dwc_to(dwc_mulr(val, dw_from(w)));
+        } else {
+          double s, c;
+          sincos(x, &s, &c);
+          const cplx e = C(c, s);
+          cplx val = C(0.0);
+          if (wantS) val = rinv * (a.ws * e);
+          if (wantK) val = val + (tau0 * rinv * rinv * rinv) * (a.wk * (e * C(-1.0, x)));
+          v = w * val;
         }
-        v = (a.unweighted ? w * a.jac[col] : w) * val;
       }
       if (col == row && a.wid != 0.0) v = v + C(a.unweighted ? a.wid : a.wid / a.jac[row], 0.0);
       Arow[col] = v;
@@ -317,7 +340,7 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   fa.pts = s->pts;
   fa.nrm = s->nrm;
   fa.jac = s->jac;
-  for (int n = 0; n < 16; ++n) fa.wgl[n] = s->gl_w[n];
+  for (int n = 0; n < 16; ++n) fa.wq[n] = s->h * 0.5 * s->gl_w[n] / s->Mt;
   fa.A = (cplx*)A_out;
   const unsigned rows_per_launch = (unsigned)((s->N < 65535) ? s->N : 65535);
   const int64_t colblocks = (s->N + 255) / 256;

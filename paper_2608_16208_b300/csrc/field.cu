@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "bie_internal.cuh"
+#include "dw.cuh"
 
 namespace bie {
 
@@ -30,7 +31,7 @@ struct FieldArgs {
   int Mt;
   double h, k, eta;
   int rep, far, unweighted;
-  double wgl[16];
+  double wq[16];        // (h/2) w_n / Mt: Gauss-Legendre weight on [-1, 1] times the panel and trapezoid factors
   const double* pts;
   const double* nrm;
   const double* jac;
@@ -39,43 +40,86 @@ struct FieldArgs {
   double2* out;
 };
 
-// One CTA per evaluation point; threads over the surface nodes.
+// |phase| below which the kernel's e^{i phase} goes through the double-word sin/cos
+constexpr double kFieldDwMaxPhase = 4096.0;
+
+// One CTA per evaluation point; threads over the surface nodes.  FP64 for the differences, rho^2,
+// rsqrt and the phase; the sin/cos series, the kernel, its product with the density and the
+// per-thread sums in double words (a thread adds about N / 256 terms, so the sloppy sums stay near
+// 1e-13 of the sum of magnitudes); the block reduction in FP64.
 __global__ void field_kernel(const FieldArgs a) {
   const int64_t p = blockIdx.x;
   const double x = a.tgt[3 * p], y = a.tgt[3 * p + 1], z = a.tgt[3 * p + 2];
-  double re = 0, im = 0;
+  const float4 ceta = mkc(dw_from(0.0), dw_from(-a.eta));   // -i eta
+  float4 acc = dwc_zero();
+  double re = 0, im = 0;   // terms whose phase is beyond the double-word sin/cos range
   for (int64_t i = threadIdx.x; i < a.N; i += blockDim.x) {
     const int n = (int)((i / a.Mt) % 16);
-    const double w = a.h * 0.5 * a.wgl[n] / a.Mt;
+    const double w = a.unweighted ? a.wq[n] * a.jac[i] : a.wq[n];
     const double yx = a.pts[3 * i], yy = a.pts[3 * i + 1], yz = a.pts[3 * i + 2];
     const double nx = a.nrm[3 * i], ny = a.nrm[3 * i + 1], nz = a.nrm[3 * i + 2];
-    cplx kern;
+    const double2 d = a.dens[i];
     if (!a.far) {
       const double dx = yx - x, dy = yy - y, dz = yz - z;
-      const double rho = sqrt(dx * dx + dy * dy + dz * dz);
-      const cplx e = cexpi(a.k * rho);
-      const cplx sl = e * (1.0 / rho);
-      if (a.rep == BIE_OP_S) {
-        kern = sl;
-      } else {
-        const double tau0 = nx * dx + ny * dy + nz * dz;
-        kern = (tau0 / (rho * rho * rho)) * (e * C(-1.0, a.k * rho));
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = rsqrt(r2);
+      const double ph = a.k * (r2 * rinv);
+      const double tau0 = a.rep == BIE_OP_S ? 0.0 : nx * dx + ny * dy + nz * dz;
+      if (ph < kFieldDwMaxPhase) {
+        float2 sn, cs;
+        dw_sincos(ph, &sn, &cs);
+        const float2 ri = dw_from(rinv);
+        const float4 sl = mkc(dw_mul(cs, ri), dw_mul(sn, ri));   // e^{ik rho} / rho
+        float4 kern = sl;
+        if (a.rep != BIE_OP_S) {
+          // tau0 / rho^3 e^{ik rho} (ik rho - 1)
+          const float2 xd = dw_from(ph);
+          const float2 f = dw_mul(dw_from(tau0), dw_mul(ri, dw_mul(ri, ri)));
+          kern = dwc_mulr(mkc(dw_sub(dw_neg(cs), dw_mul(xd, sn)), dw_sub(dw_mul(xd, cs), sn)), f);
+          if (a.rep == BIE_OP_CFIE) kern = dwc_add(kern, dwc_mul(ceta, sl));
+        }
+        acc = dwc_add(acc, dwc_mulr(dwc_mul(kern, dwc_from(C(d.x, d.y))), dw_from(w)));
+        continue;
+      }
+      const double rho = r2 * rinv;
+      const cplx e = cexpi(ph);
+      const cplx sl = e * rinv;
+      cplx kern = sl;
+      if (a.rep != BIE_OP_S) {
+        kern = (tau0 * rinv * rinv * rinv) * (e * C(-1.0, a.k * rho));
         if (a.rep == BIE_OP_CFIE) kern = kern + C(0.0, -a.eta) * sl;
       }
+      const cplx v = w * (kern * C(d.x, d.y));
+      re += v.re;
+      im += v.im;
     } else {  // far-field pattern in direction (x, y, z) (unit vector)
-      const cplx e = cexpi(-a.k * (x * yx + y * yy + z * yz));
-      if (a.rep == BIE_OP_S) {
-        kern = e;
-      } else {
-        kern = C(0.0, -a.k * (x * nx + y * ny + z * nz)) * e;
+      const double ph = -a.k * (x * yx + y * yy + z * yz);
+      const double kn = -a.k * (x * nx + y * ny + z * nz);
+      if (fabs(ph) < kFieldDwMaxPhase) {
+        float2 sn, cs;
+        dw_sincos(ph, &sn, &cs);
+        const float4 e = mkc(cs, sn);
+        float4 kern = e;
+        if (a.rep != BIE_OP_S) {
+          kern = dwc_mul(mkc(dw_from(0.0), dw_from(kn)), e);   // -i k (d . nu) e
+          if (a.rep == BIE_OP_CFIE) kern = dwc_add(kern, dwc_mul(ceta, e));
+        }
+        acc = dwc_add(acc, dwc_mulr(dwc_mul(kern, dwc_from(C(d.x, d.y))), dw_from(w)));
+        continue;
+      }
+      const cplx e = cexpi(ph);
+      cplx kern = e;
+      if (a.rep != BIE_OP_S) {
+        kern = C(0.0, kn) * e;
         if (a.rep == BIE_OP_CFIE) kern = kern + C(0.0, -a.eta) * e;
       }
+      const cplx v = w * (kern * C(d.x, d.y));
+      re += v.re;
+      im += v.im;
     }
-    const double2 d = a.dens[i];
-    const cplx v = (a.unweighted ? w * a.jac[i] : w) * (kern * C(d.x, d.y));
-    re += v.re;
-    im += v.im;
   }
+  re += dw_to(cre(acc));
+  im += dw_to(cim(acc));
   for (int o = 16; o; o >>= 1) {
     re += __shfl_xor_sync(0xffffffffu, re, o);
     im += __shfl_xor_sync(0xffffffffu, im, o);
@@ -122,7 +166,7 @@ bie_status bie_field_eval(bie_ctx ctx, bie_surface s, int rep_flags, double k, d
   a.unweighted = (rep_flags & BIE_UNWEIGHTED) ? 1 : 0;
   a.jac = s->jac;
   a.far = far_field ? 1 : 0;
-  for (int i = 0; i < 16; ++i) a.wgl[i] = s->gl_w[i];
+  for (int i = 0; i < 16; ++i) a.wq[i] = s->h * 0.5 * s->gl_w[i] / s->Mt;
   a.pts = s->pts;
   a.nrm = s->nrm;
   a.dens = (const double2*)density;

@@ -113,3 +113,20 @@ def test_solver_reports_nonconvergence(bie, ctx, ggq):
     g = bie.rhs(s, 0, [0, 0, 1], 1.0)
     with pytest.raises(bie.BieError):
         bie.solve(ctx, A, g, tol=1e-14, restart=2, maxit=3)
+
+
+@pytest.mark.parametrize("rep", ["S", "K", "CFIE"])
+@pytest.mark.parametrize("far", [False, True])
+def test_field_eval_matches_oracle(bie, ctx, ggq, rep, far):
+    """The layer potentials (and far-field patterns) of a random density against the oracle's sums.
+    The kernel sums in double words, so the bound (1e-11 of the largest value) sits well inside the
+    1e-8 required of scattered fields; a dropped term or a wrong sign misses it by orders."""
+    surface, Np, Mt, k = wl.bumpy(), 4, 32, 3.0
+    s = bie.Surface(ctx, surface, Np, Mt, ggq)
+    dens = wl.random_complex((s.N,), 4, 1)
+    op = {"S": bie.OP_S, "K": bie.OP_K, "CFIE": bie.OP_CFIE}[rep]
+    pts = wl.Stream(0, 9).directions(8) if far else wl.exterior_points(8, 2.5)
+    got = bie.field_eval(s, op, k, torch.from_numpy(dens).cuda(), pts, far_field=far).cpu().numpy()
+    fn = ny.far_field if far else ny.field
+    ref = fn(surface, Np, Mt, k, dens, pts, rep=rep)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref)), np.max(np.abs(got - ref)) / np.max(np.abs(ref))
