@@ -35,33 +35,38 @@ struct FarArgs {
 
 // k rho below which the entry's phase goes through the double-word sin/cos (FP64 reduction by pi/2)
 constexpr double kFarDwMaxPhase = 4096.0;
+// rows per thread of the far fill: a thread keeps its column's node, normal and weight in registers
+constexpr int kFarRows = 16;
 
-// One thread per (row, column); grid-stride over the N x N entries, rows in blockIdx.y chunks.
-// FP64 for the differences, rho^2, rsqrt and k rho (the phase keeps FP64 accuracy); the sin/cos
-// series and the products of the entry in double words, so that the FP64 pipe carries about a third
-// of the instructions of an all-FP64 entry.
+// Thread per column, kFarRows consecutive rows per block (row tiles grid-strided over blockIdx.y);
+// a row's 256 entries of a block are stored contiguously.  FP64 for the differences, rho^2, rsqrt
+// and k rho (the phase keeps FP64 accuracy); the sin/cos series and the products of the entry in
+// double words, so that the FP64 pipe carries about a third of the instructions of an all-FP64 entry.
 __global__ void far_fill_kernel(const FarArgs a) {
-  const int64_t N = a.N;
-  const int64_t per_panel = (int64_t)16 * a.Mt;
+  const int N = (int)a.N;
+  const int per_panel = 16 * a.Mt;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= N) return;
   const bool wantS = a.ws.re != 0.0 || a.ws.im != 0.0;
   const bool wantK = a.wk.re != 0.0 || a.wk.im != 0.0;
   const float4 wsd = dwc_from(a.ws), wkd = dwc_from(a.wk);
-  for (int64_t row = blockIdx.y; row < N; row += gridDim.y) {
-    const double xx = a.pts[3 * row], xy = a.pts[3 * row + 1], xz = a.pts[3 * row + 2];
-    const int jrow = (int)(row / per_panel);
-    cplx* Arow = a.A + row * N;
-    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < N; col += (int64_t)gridDim.x * blockDim.x) {
-      const int jcol = (int)(col / per_panel);
+  const int jcol = col / per_panel;
+  const int n = (col / a.Mt) & 15;
+  const double w = a.unweighted ? a.wq[n] * a.jac[col] : a.wq[n];
+  const float2 wd = dw_from(w);
+  const double sx = a.pts[3 * col], sy = a.pts[3 * col + 1], sz = a.pts[3 * col + 2];
+  const double nx = a.nrm[3 * col], ny = a.nrm[3 * col + 1], nz = a.nrm[3 * col + 2];
+  for (int r0 = blockIdx.y * kFarRows; r0 < N; r0 += gridDim.y * kFarRows) {
+    const int rend = min(r0 + kFarRows, N);
+    for (int row = r0; row < rend; ++row) {
+      const int jrow = row / per_panel;
       cplx v = C(0.0);
       if (abs(jcol - jrow) >= 2) {
-        const double yx = a.pts[3 * col] - xx, yy = a.pts[3 * col + 1] - xy, yz = a.pts[3 * col + 2] - xz;
+        const double yx = sx - a.pts[3 * row], yy = sy - a.pts[3 * row + 1], yz = sz - a.pts[3 * row + 2];
         const double r2 = yx * yx + yy * yy + yz * yz;
         const double rinv = rsqrt(r2);
-        const double rho = r2 * rinv;
-        const double x = a.k * rho;
-        const int n = (int)((col / a.Mt) % 16);
-        const double w = a.unweighted ? a.wq[n] * a.jac[col] : a.wq[n];
-        const double tau0 = wantK ? a.nrm[3 * col] * yx + a.nrm[3 * col + 1] * yy + a.nrm[3 * col + 2] * yz : 0.0;
+        const double x = a.k * (r2 * rinv);
+        const double tau0 = wantK ? nx * yx + ny * yy + nz * yz : 0.0;
         if (x < kFarDwMaxPhase) {
           float2 sn, cs;
           dw_sincos(x, &sn, &cs);
@@ -75,7 +80,7 @@ __global__ void far_fill_kernel(const FarArgs a) {
             const float4 g = mkc(dw_sub(dw_neg(cs), dw_mul(xd, sn)), dw_sub(dw_mul(xd, cs), sn));
             val = dwc_add(val, dwc_mul(wkd, dwc_mulr(g, f)));
           }
-          v = dwc_to(dwc_mulr(val, dw_from(w)));
+          v = dwc_to(dwc_mulr(val, wd));
         } else {
           double s, c;
           sincos(x, &s, &c);
@@ -87,7 +92,7 @@ __global__ void far_fill_kernel(const FarArgs a) {
         }
       }
       if (col == row && a.wid != 0.0) v = v + C(a.unweighted ? a.wid : a.wid / a.jac[row], 0.0);
-      Arow[col] = v;
+      a.A[(int64_t)row * N + col] = v;
     }
   }
 }
@@ -342,9 +347,8 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   fa.jac = s->jac;
   for (int n = 0; n < 16; ++n) fa.wq[n] = s->h * 0.5 * s->gl_w[n] / s->Mt;
   fa.A = (cplx*)A_out;
-  const unsigned rows_per_launch = (unsigned)((s->N < 65535) ? s->N : 65535);
-  const int64_t colblocks = (s->N + 255) / 256;
-  dim3 grid((unsigned)(colblocks < 64 ? colblocks : 64), rows_per_launch);
+  const int64_t row_tiles = (s->N + kFarRows - 1) / kFarRows;
+  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)(row_tiles < 65535 ? row_tiles : 65535));
   far_fill_kernel<<<grid, 256, 0, ctx->stream>>>(fa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "far_fill_kernel");
