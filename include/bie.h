@@ -130,7 +130,10 @@ const double* bie_surface_jacobians(bie_surface s);
  *   modes_out [dev] double2[n_pairs][n_kernels][Mth+1], kernels in bit order
  *   k > 0 wavenumber.
  * Errors: BIE_EINVAL (bad sizes/pointers; a pair whose source panel does not
- * exist yields zeros and BIE_EINVAL after the next bie_ctx_sync), BIE_ECUDA.   */
+ * exist yields zeros and BIE_EINVAL after the next bie_ctx_sync), BIE_ECUDA.
+ * Not for stream capture: the call may grow its device buffers (cudaMalloc,
+ * with a stream synchronisation) and sets the kernels' shared-memory launch
+ * attribute for this surface's Mth.  Capture bie_batch_run instead.           */
 bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
                             const int64_t* pair_row, const int32_t* pair_src, int64_t n_pairs,
                             double* modes_out);
@@ -227,7 +230,8 @@ bie_status bie_assemble_near(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
  * run.  Asynchronous on the ctx stream either way: the band is complete once
  * the ctx stream passes this call (bie_ctx_sync).  Pageable host memory is
  * refused (BIE_EINVAL).  The caller keeps the buffer alive until then.
- * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.                                  */
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.  Not for stream capture (as
+ * bie_kernel_modes; it also creates a stream and events for the host copies). */
 bie_status bie_assemble_near_band(bie_ctx ctx, bie_surface s, unsigned kernels, double k,
                                   double ws_re, double ws_im, double wk_re, double wk_im,
                                   double* band_out);
