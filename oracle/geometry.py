@@ -11,9 +11,15 @@ generators in ``workloads``):
       r = h(t, th) (sin t cos th, sin t sin th, cos t),
       h = 1 + sum_i c_i sin^p_i(t) cos^q_i(t) T_i(m_i th),
       T = cos if s_i == 0 else sin,  t in [0, pi]
+  {"kind": "torus", "a": a, "b": b, "c": c, "R": R, "eps": eps, "m": m}
+      r = (a w cos t, b w sin t, c sin th),  w = R + cos th + eps cos(m t),
+      t in [0, 2 pi] with r(0, th) = r(2 pi, th): a torus-like surface (the
+      wiggly torus of Section 5, Example 3, has a, b, c, R, eps, m =
+      1.2, 1, 1.7, 2, 0.25, 5)
 
-Both satisfy assumptions (i)-(iii) of Section 2 at every quadrature node
-(J vanishes only at the poles t = 0, pi, which are never nodes).
+All satisfy assumptions (i)-(iii) of Section 2 at every quadrature node (J
+vanishes only at the poles t = 0, pi of the first two, which are never nodes;
+it does not vanish on the torus).
 
 Every function accepts real t and real or complex theta (complex theta is
 the analytic continuation used to locate the complex root of rho^2,
@@ -24,7 +30,12 @@ import numpy as np
 
 def parameter_length(surface):
     """Length L of the t-interval [0, L] (Section 2)."""
-    return np.pi
+    return 2 * np.pi if surface["kind"] == "torus" else np.pi
+
+
+def is_periodic(surface):
+    """Torus-like surface (r(0, th) = r(L, th)): the first and last panels are adjacent (Section 3.1)."""
+    return surface["kind"] == "torus"
 
 
 def _sc_power(st, ct, p, q):
@@ -106,6 +117,20 @@ def evaluate(surface, t, th):
         rtt = H(htt) * e + 2 * H(ht) * et + H(h) * ett
         rtth = H(htth) * e + H(ht) * eth + H(hth) * et + H(h) * etth
         rthth = H(hthth) * e + 2 * H(hth) * eth + H(h) * ethth
+        return r, rt, rth, rtt, rtth, rthth
+    if surface["kind"] == "torus":
+        a, b, c = surface["a"], surface["b"], surface["c"]
+        m, eps = float(surface["m"]), surface["eps"]
+        smt, cmt = np.sin(m * t), np.cos(m * t)
+        w = surface["R"] + cp + eps * cmt
+        wt, wth = -eps * m * smt + z, -sp
+        wtt, wthth = -eps * m * m * cmt + z, -cp
+        r = np.stack([a * w * ct, b * w * st, c * sp], -1)
+        rt = np.stack([a * (wt * ct - w * st), b * (wt * st + w * ct), z], -1)
+        rth = np.stack([a * wth * ct, b * wth * st, c * cp], -1)
+        rtt = np.stack([a * (wtt * ct - 2 * wt * st - w * ct), b * (wtt * st + 2 * wt * ct - w * st), z], -1)
+        rtth = np.stack([-a * wth * st, b * wth * ct, z], -1)
+        rthth = np.stack([a * wthth * ct, b * wthth * st, -c * sp], -1)
         return r, rt, rth, rtt, rtth, rthth
     raise ValueError("unknown surface kind %r" % surface["kind"])
 

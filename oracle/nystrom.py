@@ -5,7 +5,10 @@ TEST INFRASTRUCTURE ONLY.  Plain FP64 numpy.
 Unknowns are the weighted densities phi~ = phi J (Section 3, Eq. (S:para))
 at the nodes (t_i^n, th_l): panel i = 0..Np-1 (uniform panels of [0, L]),
 Gauss-Legendre node n = 0..15, th_l = 2 pi l / Mth.  Flat index
-(i*16 + n)*Mth + l.
+(i*16 + n)*Mth + l.  On a torus-like surface (r(0, th) = r(L, th)) panel
+indices are cyclic: panels 0 and Np-1 are adjacent (Section 3.1, Remark), and
+the source nodes of a wrapped neighbour keep their unwrapped t (t < 0 or > L),
+the surface being L-periodic in t.
 
 Row of target (t_j^l, th_i), Section 3.1 Eq. (S123) and Section 3.4:
   far panels |i' - j| >= 2  (Eq. (S1) x Eq. (Sphi:sm)):
@@ -83,15 +86,15 @@ def kernel_values(surface, x, t_s, th_s, k, kind, nu_x=None):
     return tau0 * np.exp(1j * k * rho) * (1j * k * rho - 1) / rho ** 3
 
 
-def near_pairs(Np, Mt, rows, ggq_x):
+def near_pairs(Np, Mt, rows, ggq_x, L=np.pi, periodic=False):
     """Near pairs of the given target rows: list of (row, delta, g) plus t, th, t_s."""
-    t_nodes, h = nodes(Np)
+    t_nodes, h = nodes(Np, L)
     out = []
     for r in rows:
         j, l, i = r // (16 * Mt), (r // Mt) % 16, r % Mt
         for di, delta in enumerate((-1, 0, 1)):
             ip = j + delta
-            if ip < 0 or ip >= Np:
+            if not periodic and (ip < 0 or ip >= Np):
                 continue
             for g in range(16):
                 ts = (ip + 0.5) * h + (h / 2) * ggq_x[di, l, g]
@@ -101,7 +104,8 @@ def near_pairs(Np, Mt, rows, ggq_x):
 
 def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=512):
     """Dense rows of the S and/or K matrices: dict kind -> (len(rows), N)."""
-    t_nodes, h = nodes(Np)
+    L, periodic = geo.parameter_length(surface), geo.is_periodic(surface)
+    t_nodes, h = nodes(Np, L)
     N = 16 * Np * Mt
     th = 2 * np.pi * np.arange(Mt) / Mt
     rows = np.asarray(rows)
@@ -115,14 +119,15 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=51
     X = geo.evaluate(surface, t_nodes[rows // Mt], th[rows % Mt])[0]
     for c0 in range(0, len(rows), 64):
         sl = slice(c0, c0 + 64)
-        far = np.abs(src_panel[None, :] - tgt_panel[sl, None]) >= 2
+        dp = np.abs(src_panel[None, :] - tgt_panel[sl, None])
+        far = (np.minimum(dp, Np - dp) if periodic else dp) >= 2
         for kd in kinds:
             with np.errstate(divide="ignore", invalid="ignore"):     # the self point is masked out
                 vals = kernel_values(surface, X[sl, None, :], TS[None, :], THS[None, :], k, kd)
             out[kd][sl] = np.where(far, wq[None, :] * vals, 0.0)
     # near panels: GGQ x Lagrange interpolation x Parseval weights
     coef = (h / 2) * ggq_w[..., None] * lagrange(ggq_x.ravel()).reshape(3, 16, 16, 16)
-    pairs = near_pairs(Np, Mt, rows, ggq_x)
+    pairs = near_pairs(Np, Mt, rows, ggq_x, L, periodic)
     row_pos = {r: p for p, r in enumerate(rows)}
     for c0 in range(0, len(pairs), chunk):
         block = pairs[c0:c0 + chunk]
@@ -133,7 +138,7 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=51
         tht = np.array([p[4] for p in block])
         ts = np.array([p[5] for p in block])
         l = (r // Mt) % 16
-        ip = r // (16 * Mt) + di - 1
+        ip = (r // (16 * Mt) + di - 1) % Np
         pos = np.array([row_pos[v] for v in r])
         cols = ip[:, None, None] * 16 * Mt + np.arange(16)[None, :, None] * Mt + np.arange(Mt)[None, None, :]
         modes = km.method_modes(surface, t, tht, ts, Mt, k, kernels=tuple(kinds))
@@ -153,7 +158,7 @@ def operator_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, op="S", eta=None):
     A = blocks["K"]
     if op == "K":
         return A
-    t_nodes, _ = nodes(Np)
+    t_nodes, _ = nodes(Np, geo.parameter_length(surface))
     rows = np.asarray(rows)
     th = 2 * np.pi * np.arange(Mt) / Mt
     tr = t_nodes[rows // Mt]
@@ -166,7 +171,7 @@ def operator_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, op="S", eta=None):
 
 
 def boundary_nodes(surface, Np, Mt):
-    t_nodes, h = nodes(Np)
+    t_nodes, h = nodes(Np, geo.parameter_length(surface))
     th = 2 * np.pi * np.arange(Mt) / Mt
     T = np.repeat(t_nodes, Mt)
     TH = np.tile(th, 16 * Np)
@@ -190,7 +195,7 @@ def point_source_rhs(surface, Np, Mt, k, src):
 
 def field(surface, Np, Mt, k, density, points, rep="S", eta=None):
     """u(x) at points off the surface (Section 3.4: GL in t x trapezoid in theta)."""
-    t_nodes, h = nodes(Np)
+    t_nodes, h = nodes(Np, geo.parameter_length(surface))
     r, nu, J, T, TH = boundary_nodes(surface, Np, Mt)
     w = np.repeat(np.tile(WG, Np), Mt) * (h / 2) / Mt
     out = []
@@ -211,7 +216,7 @@ def field(surface, Np, Mt, k, density, points, rep="S", eta=None):
 
 def far_field(surface, Np, Mt, k, density, dirs, rep="S", eta=None):
     """u_inf(d): u ~ e^{ik|x|}/|x| u_inf."""
-    t_nodes, h = nodes(Np)
+    t_nodes, h = nodes(Np, geo.parameter_length(surface))
     r, nu, J, T, TH = boundary_nodes(surface, Np, Mt)
     w = np.repeat(np.tile(WG, Np), Mt) * (h / 2) / Mt
     out = []

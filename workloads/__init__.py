@@ -203,3 +203,9 @@ def random_complex(shape, seed, stream):
     synthetic test matrices, where the per-value splitmix64 stream above is too slow in Python."""
     g = np.random.default_rng([int(seed), int(stream)])
     return (g.standard_normal(shape) + 1j * g.standard_normal(shape)) / np.sqrt(2.0)
+
+
+def wiggly_torus():
+    """The wiggly torus of the paper's Example 3: r = (1.2 w cos t, w sin t, 1.7 sin th),
+    w = 2 + cos th + 0.25 cos 5t, t and th in [0, 2 pi) (t periodic)."""
+    return {"kind": "torus", "a": 1.2, "b": 1.0, "c": 1.7, "R": 2.0, "eps": 0.25, "m": 5}
