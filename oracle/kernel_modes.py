@@ -7,6 +7,9 @@ of the source angle th_s:
 
   S:  e^{ik rho}/rho                               (Section 3.2, Eq. (Sphi:appr2))
   K:  alpha tau_1 - tau_3 - i beta tau_0           (Section 4, Eq. (dis:K))
+  Kp: the same with the roles of target and source exchanged in tau_j
+      (Section 4, the K' integrand): tau_0 = nu(r) . (r - r_s), the normal of
+      the target, again analytic in th_s and O(rho^2) at the target
 
 ``method_modes`` follows the paper's algorithm step by step:
   1. rho^2 on the Mth-point theta grid (Eq. (rho)); near samples use the
@@ -57,13 +60,14 @@ def sym_modes(v, M):
 
 
 def swap_convolution(f, a, A, lmax):
-    """sum_j f_j e^{-i(l-j)a} A_{|l-j|} for l = -lmax..lmax  (Eq. (convolution))."""
+    """sum_j f_j e^{-i(l-j)a} A_{|l-j|} for l = -lmax..lmax  (Eq. (convolution)),
+    written as e^{-ila} sum_j (f_j e^{ija}) A_{|l-j|} (the same sum, the phase split in two)."""
     M = (f.shape[-1] - 1) // 2
     j = np.arange(-M, M + 1)
     l = np.arange(-lmax, lmax + 1)
     d = l[:, None] - j[None, :]
-    kern = A[:, np.abs(d)] * np.exp(-1j * d[None, :, :] * a[:, None, None])
-    return np.einsum("bj,blj->bl", f, kern)
+    g = f * np.exp(1j * j[None, :] * a[:, None])
+    return np.exp(-1j * l[None, :] * a[:, None]) * np.einsum("bj,blj->bl", g, A[:, np.abs(d)])
 
 
 def linear_convolution(u, v, vmax, wmax):
@@ -195,7 +199,7 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
     s = (-np.expm1(-b))[:, None] ** 2 + 4 * q[:, None] * np.sin(phi / 2) ** 2   # Eq. (sab)
     F = np.sqrt(s / rho2)                                                     # Eq. (F-smooth)
     f = sym_modes(F, M)
-    need_k = "K" in kernels
+    need_k = "K" in kernels or "Kp" in kernels
     L = (4 if need_k else 3) * M
     A, D = sp.a_modes(b, L)
     out = {}
@@ -208,19 +212,28 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
         out["S_smooth"] = smooth
         out["S"] = out["S_sing"] + sym_modes(smooth, M)
     if need_k:
-        nu, _ = geo.normal_and_jacobian(surface, T_s, TH_s)
-        tau0 = np.sum(nu * Y, -1)
-        if np.any(near):
-            tau0[near] = geo.tau0_stable(surface, T_s[near], TH_s[near], T[near], TH[near])
         alpha, beta = alpha_beta(rho, k)
+    for kd in ("K", "Kp"):
+        if kd not in kernels:
+            continue
+        if kd == "K":   # source normal: nu(r_s) . (r_s - r)
+            nu, _ = geo.normal_and_jacobian(surface, T_s, TH_s)
+            tau0 = np.sum(nu * Y, -1)
+            if np.any(near):
+                tau0[near] = geo.tau0_stable(surface, T_s[near], TH_s[near], T[near], TH[near])
+        else:           # target normal: nu(r) . (r - r_s)
+            nu_x, _ = geo.normal_and_jacobian(surface, t, th)
+            tau0 = -np.sum(nu_x[:, None, :] * Y, -1)
+            if np.any(near):
+                tau0[near] = geo.tau0_stable(surface, T[near], TH[near], T_s[near], TH_s[near])
         T0 = sym_modes(tau0, M)
         T1 = linear_convolution(T0, R, rmax, 2 * M)                            # Eq. (tau1)
         AT1 = linear_convolution(sym_modes(alpha, M), T1, 2 * M, M)
-        T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s, f))
+        T3 = tau3_modes(tau0 * F ** 3, a, b, A, D, M, (surface, t, th, t_s, f, kd == "Kp"))
         smooth = -1j * beta * tau0
-        out["K_sing"] = AT1 - T3
-        out["K_smooth"] = smooth
-        out["K"] = out["K_sing"] + sym_modes(smooth, M)
+        out[kd + "_sing"] = AT1 - T3
+        out[kd + "_smooth"] = smooth
+        out[kd] = out[kd + "_sing"] + sym_modes(smooth, M)
     if return_details:
         out["_a"], out["_b"], out["_a0"], out["_b0"], out["_ok"] = a, b, a0, b0, ok
         out["_R"], out["_rmax"] = R, rmax
@@ -235,33 +248,43 @@ def tau3_modes(H3, a, b, A, D, M, pair):
     small = b < SMALL_B
     if np.any(small):
         i = np.nonzero(small)[0]
-        surface, t, th, t_s, f = pair
-        Ha, H1a = h3_at_root(surface, t[i], th[i], t_s[i], a[i], b[i], f[i])
+        surface, t, th, t_s, f = pair[:5]
+        target_normal = len(pair) > 5 and pair[5]
+        Ha, H1a = h3_at_root(surface, t[i], th[i], t_s[i], a[i], b[i], f[i], target_normal)
         out[i] = _tau3_translated(H3[i], h3[i], a[i], b[i], A[i], Bn[i], M, Ha, H1a)
     return out
 
 
-def h3_at_root(surface, t, th, t_s, a, b, f=None):
+def h3_at_root(surface, t, th, t_s, a, b, f=None, target_normal=False):
     """H3(a) = tau_0(a) F(a)^3 and H3'(a), evaluated at th_s = a.
 
     tau_0(a), tau_0'(a) = nu'(a) . (r_s(a) - r) and F(a) = (1 - e^{-b}) / rho(a)
     (s_{a,b}(a) = (1 - e^{-b})^2) come directly from the geometry: they are
     small (O(b^2), O(b), O(1)) and only a direct evaluation is relatively
-    accurate.  F'(a) comes from the trigonometric interpolant of F (modes f):
+    accurate.  With target_normal (the K' integrand) tau_0 = nu(r) . (r - r_s(a))
+    and tau_0'(a) = -nu(r) . r_th(t_s, a).  F'(a) comes from the trigonometric interpolant of F (modes f):
     F is smooth, while the direct form -F (rho^2)'(a) / (2 rho^2(a)) divides an
     O(b^2) dot product of O(b) vectors by rho^2 and loses digits like eps/b.
     """
     near = _near_mask(t_s, a, t, th)
     Y = geo.difference(surface, t_s, a, t, th, near)
     _, rt, rth, _, rtth, rthth = geo.evaluate(surface, t_s, a)
-    n = np.cross(rt, rth)
-    J = np.sqrt(np.sum(n * n, -1))
-    nu = n / J[:, None]
-    dn = np.cross(rtth, rth) + np.cross(rt, rthth)
-    dnu = (dn - nu * np.sum(nu * dn, -1)[:, None]) / J[:, None]
-    tau0 = np.sum(nu * Y, -1)
-    if np.any(near):
-        tau0[near] = geo.tau0_stable(surface, t_s[near], a[near], t[near], th[near])
+    if target_normal:
+        nu_x, _ = geo.normal_and_jacobian(surface, t, th)
+        tau0 = -np.sum(nu_x * Y, -1)
+        if np.any(near):
+            tau0[near] = geo.tau0_stable(surface, t[near], th[near], t_s[near], a[near])
+        dtau0 = -np.sum(nu_x * rth, -1)
+    else:
+        n = np.cross(rt, rth)
+        J = np.sqrt(np.sum(n * n, -1))
+        nu = n / J[:, None]
+        dn = np.cross(rtth, rth) + np.cross(rt, rthth)
+        dnu = (dn - nu * np.sum(nu * dn, -1)[:, None]) / J[:, None]
+        tau0 = np.sum(nu * Y, -1)
+        if np.any(near):
+            tau0[near] = geo.tau0_stable(surface, t_s[near], a[near], t[near], th[near])
+        dtau0 = np.sum(dnu * Y, -1)
     rho2 = np.sum(Y * Y, -1)
     F = -np.expm1(-b) / np.sqrt(rho2)
     if f is None:
@@ -270,7 +293,6 @@ def h3_at_root(surface, t, th, t_s, a, b, f=None):
         M = (f.shape[-1] - 1) // 2
         j = np.arange(-M, M + 1)
         dF = np.real(np.sum(f * (1j * j)[None, :] * np.exp(1j * j[None, :] * a[:, None]), -1))
-    dtau0 = np.sum(dnu * Y, -1)
     return tau0 * F ** 3, dtau0 * F ** 3 + 3 * tau0 * F ** 2 * dF
 
 
@@ -333,12 +355,19 @@ def definition_modes(surface, t, th, t_s, M, k, kernel="S", n_start=None, tol=1e
         rho = np.sqrt(np.sum(Y * Y, -1))
         if kernel == "S":
             f = np.exp(1j * k * rho) / rho
-        else:
+        elif kernel == "K":
             nu, _ = geo.normal_and_jacobian(surface, np.full(n, t_s), thq)
             tau0 = np.sum(nu * Y, -1)
             if np.any(near):
                 tau0[near] = geo.tau0_stable(surface, np.full(near.sum(), t_s), thq[near],
                                              np.full(near.sum(), t), np.full(near.sum(), th))
+            f = tau0 * np.exp(1j * k * rho) * (1j * k * rho - 1) / rho ** 3
+        else:   # Kp: the target's normal
+            nu_x, _ = geo.normal_and_jacobian(surface, t, th)
+            tau0 = -(Y @ nu_x)
+            if np.any(near):
+                tau0[near] = geo.tau0_stable(surface, np.full(near.sum(), t), np.full(near.sum(), th),
+                                             np.full(near.sum(), t_s), thq[near])
             f = tau0 * np.exp(1j * k * rho) * (1j * k * rho - 1) / rho ** 3
         c = np.fft.fft(f) / n
         m = np.arange(-M, M + 1)

@@ -21,13 +21,18 @@ Row of target (t_j^l, th_i), Section 3.1 Eq. (S123) and Section 3.4:
       W_{l'} = (1/Mth) [ sum_{|m|<M} K_m e^{i m th_l'} + (K_M + K_{-M})/2 (-1)^{l'} ],
   plus, for the smooth part f (i sin(k rho)/rho, -i beta tau_0), f(th_l')/Mth.
 Kernels G~: S -> e^{ik rho}/rho;  K -> tau_0 e^{ik rho}(ik rho - 1)/rho^3
-(= alpha tau_1 - tau_3 - i beta tau_0, Section 4).
+(= alpha tau_1 - tau_3 - i beta tau_0, Section 4) with tau_0 = nu(y) . (y - x);
+Kp (the adjoint K') -> the same with tau_0 = nu(x) . (x - y), the target's
+normal (Eq. (adl)).
 
 Operators acting on the weighted density (identity = diag(1/J)):
   "S"       S                     (Eq. (bie:S))
   "K"       K
   "K+I", "K-I"                    (Eq. (bie:Kie))
+  "Kp", "Kp+I", "Kp-I"            (Eq. (bie:Kpie): + interior, - exterior Neumann)
   "CFIE"    I + K - i eta S       (exterior Dirichlet, combined field)
+These are the paper's operators, which carry a factor 2 (Eqs. (sl), (adl)):
+G~ omits 1/(4 pi) and the trapezoid weight 1/Mth omits 2 pi.
 """
 import numpy as np
 
@@ -81,8 +86,11 @@ def kernel_values(surface, x, t_s, th_s, k, kind, nu_x=None):
     rho = np.sqrt(np.sum(Y * Y, -1))
     if kind == "S":
         return np.exp(1j * k * rho) / rho
-    nu, _ = geo.normal_and_jacobian(surface, t_s, th_s)
-    tau0 = np.sum(nu * Y, -1)
+    if kind == "Kp":
+        tau0 = -np.sum(nu_x * Y, -1)
+    else:
+        nu, _ = geo.normal_and_jacobian(surface, t_s, th_s)
+        tau0 = np.sum(nu * Y, -1)
     return tau0 * np.exp(1j * k * rho) * (1j * k * rho - 1) / rho ** 3
 
 
@@ -102,8 +110,11 @@ def near_pairs(Np, Mt, rows, ggq_x, L=np.pi, periodic=False):
     return out
 
 
-def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=512):
-    """Dense rows of the S and/or K matrices: dict kind -> (len(rows), N)."""
+def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=None):
+    """Dense rows of the S and/or K matrices: dict kind -> (len(rows), N).  Near pairs go through
+    the per-pair pipeline in batches of `chunk` (default: about 200 MB of convolution table)."""
+    if chunk is None:
+        chunk = int(max(256, min(4096, 2e8 / (8 * (6 * Mt + 1) * (Mt + 1)))))
     L, periodic = geo.parameter_length(surface), geo.is_periodic(surface)
     t_nodes, h = nodes(Np, L)
     N = 16 * Np * Mt
@@ -117,13 +128,15 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=51
     wq = np.repeat(np.tile(WG, Np), Mt) * (h / 2) / Mt
     tgt_panel = rows // (16 * Mt)
     X = geo.evaluate(surface, t_nodes[rows // Mt], th[rows % Mt])[0]
+    NUX = geo.normal_and_jacobian(surface, t_nodes[rows // Mt], th[rows % Mt])[0] if "Kp" in kinds else None
     for c0 in range(0, len(rows), 64):
         sl = slice(c0, c0 + 64)
         dp = np.abs(src_panel[None, :] - tgt_panel[sl, None])
         far = (np.minimum(dp, Np - dp) if periodic else dp) >= 2
         for kd in kinds:
             with np.errstate(divide="ignore", invalid="ignore"):     # the self point is masked out
-                vals = kernel_values(surface, X[sl, None, :], TS[None, :], THS[None, :], k, kd)
+                vals = kernel_values(surface, X[sl, None, :], TS[None, :], THS[None, :], k, kd,
+                                     NUX[sl, None, :] if kd == "Kp" else None)
             out[kd][sl] = np.where(far, wq[None, :] * vals, 0.0)
     # near panels: GGQ x Lagrange interpolation x Parseval weights
     coef = (h / 2) * ggq_w[..., None] * lagrange(ggq_x.ravel()).reshape(3, 16, 16, 16)
@@ -151,19 +164,20 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=51
 
 def operator_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, op="S", eta=None):
     """Rows of the operator matrix acting on the weighted density."""
-    kinds = {"S": ("S",), "K": ("K",), "K+I": ("K",), "K-I": ("K",), "CFIE": ("S", "K")}[op]
+    kinds = {"S": ("S",), "K": ("K",), "K+I": ("K",), "K-I": ("K",), "CFIE": ("S", "K"),
+             "Kp": ("Kp",), "Kp+I": ("Kp",), "Kp-I": ("Kp",)}[op]
     blocks = assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds)
     if op == "S":
         return blocks["S"]
-    A = blocks["K"]
-    if op == "K":
+    A = blocks[kinds[0] if op.startswith("Kp") else "K"]
+    if op in ("K", "Kp"):
         return A
     t_nodes, _ = nodes(Np, geo.parameter_length(surface))
     rows = np.asarray(rows)
     th = 2 * np.pi * np.arange(Mt) / Mt
     tr = t_nodes[rows // Mt]
     _, J = geo.normal_and_jacobian(surface, tr, th[rows % Mt])
-    sign = {"K+I": 1.0, "K-I": -1.0, "CFIE": 1.0}[op]
+    sign = {"K+I": 1.0, "K-I": -1.0, "Kp+I": 1.0, "Kp-I": -1.0, "CFIE": 1.0}[op]
     A[np.arange(len(rows)), rows] += sign / J
     if op == "CFIE":
         A = A - 1j * (k if eta is None else eta) * blocks["S"]
@@ -191,6 +205,14 @@ def point_source_rhs(surface, Np, Mt, k, src):
     r = boundary_nodes(surface, Np, Mt)[0]
     d = np.sqrt(np.sum((r - np.asarray(src)) ** 2, -1))
     return np.exp(1j * k * d) / (4 * np.pi * d)
+
+
+def normal_derivative_rhs(surface, Np, Mt, k, src):
+    """g = d/dnu(x) G(x; x_src) on the nodes (Neumann data of the point-source field)."""
+    r, nu, _, _, _ = boundary_nodes(surface, Np, Mt)
+    Y = r - np.asarray(src)
+    d = np.sqrt(np.sum(Y * Y, -1))
+    return np.sum(nu * Y, -1) * np.exp(1j * k * d) * (1j * k * d - 1) / (4 * np.pi * d ** 3)
 
 
 def field(surface, Np, Mt, k, density, points, rep="S", eta=None):

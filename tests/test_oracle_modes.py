@@ -1,6 +1,6 @@
 """Pins of the oracle's per-pair pipeline (Sections 3.2-3.3, 4):
   * the sphere through the general path, where everything has a closed form;
-  * the plain definition (brute-force trapezoid, no singularity swapping);
+  * the plain definition (brute-force trapezoid, no singularity swapping), for S, K and K';
   * invariants the paper states: Eq. (iter:formula), conjugate symmetry;
   * a planted mistake that the pins must catch."""
 import numpy as np
@@ -42,11 +42,10 @@ def test_sphere_special_case_closed_form():
 @pytest.mark.parametrize("dt", [2e-4, 0.006, 0.05, 0.3])
 def test_method_matches_definition(surface, Mt, k, dt):
     t, th = 1.1, 2 * np.pi * 5 / Mt
-    out = km.method_modes(surface, np.array([t]), np.array([th]), np.array([t + dt]), Mt, k, ("S", "K"))
-    dS, _ = km.definition_modes(surface, t, th, t + dt, Mt // 2, k, "S")
-    dK, _ = km.definition_modes(surface, t, th, t + dt, Mt // 2, k, "K")
-    assert _rel(out["S"][0], dS) <= 1e-12
-    assert _rel(out["K"][0], dK) <= 1e-12
+    out = km.method_modes(surface, np.array([t]), np.array([th]), np.array([t + dt]), Mt, k, ("S", "K", "Kp"))
+    for kd in ("S", "K", "Kp"):
+        d, _ = km.definition_modes(surface, t, th, t + dt, Mt // 2, k, kd)
+        assert _rel(out[kd][0], d) <= 1e-12, kd
 
 
 def test_recurrence_identity_and_conjugate_symmetry():

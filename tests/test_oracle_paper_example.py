@@ -1,8 +1,9 @@
 """The oracle against the errors the paper prints for its Examples 1 and 3 (Section 5, Tables
 "tab:ex1" and "tab:ex3"): interior Dirichlet problems whose exact solution is the field of a point
 source outside, on the ellipsoid with semi-axes (1, 2, 3) and on the wiggly torus, solved through
-the single layer (S phi = g) and through the double layer ((K - 1/2) psi = g), at the paper's own
-(Np, 2M).  The torus case exercises the torus-like adjacency of Section 3.1 (Remark: the first and
+the single layer (S phi = g) and through the double layer ((K - 1/2) psi = g), and the interior
+Neumann problem through the adjoint double layer ((K' + 1/2) phi = dG/dnu, u = S phi), at the
+paper's own (Np, 2M).  The torus case exercises the torus-like adjacency of Section 3.1 (Remark: the first and
 last panels are neighbours); treating it as an open surface raises its E from 6e-11 to 6e-7.
 
 The paper's E divides the l2 error over the test region's grid points by their number, and the
@@ -11,7 +12,8 @@ the paper's test ball the oracle's E must stay within 3 times the printed value.
 wrong sign anywhere in the quadrature misses this by orders of magnitude.
 
 The oracle's kernels omit 1/(4 pi) and its trapezoid weight omits 2 pi, so its S and K are twice the
-operators with G = e^{ikr}/(4 pi r); "K-I" is then 2 (K - 1/2), and the field routine returns u."""
+operators with G = e^{ikr}/(4 pi r), which are the paper's (Eqs. (sl), (adl) carry the factor 2):
+"K-I" is 2 (K - 1/2), "Kp+I" is 2 (K' + 1/2), and the field routine returns u."""
 import os
 
 import numpy as np
@@ -32,7 +34,8 @@ EXAMPLES = {
 
 def printed(example):
     rows = np.loadtxt(os.path.join(HERE, "golden", EXAMPLES[example][1]))
-    return {int(r[0]): {"S": (int(r[1]), int(r[2]), r[3]), "K": (int(r[4]), int(r[5]), r[6])} for r in rows}
+    return {int(r[0]): {"S": (int(r[1]), int(r[2]), r[3]), "K": (int(r[4]), int(r[5]), r[6]),
+                        "Kp": (int(r[7]), int(r[8]), r[9])} for r in rows}
 
 
 def ball_points(center, radius, n=20):
@@ -45,16 +48,22 @@ def ball_points(center, radius, n=20):
     return np.array(pts)
 
 
-@pytest.mark.parametrize("example,k,kind", [(1, 1, "S"), (1, 4, "S"), (1, 1, "K"), (3, 1, "S")])
+# (operator, right-hand side, representation) per column of the tables
+PROBLEMS = {"S": ("S", ny.point_source_rhs, "S"), "K": ("K-I", ny.point_source_rhs, "K"),
+            "Kp": ("Kp+I", ny.normal_derivative_rhs, "S")}
+
+
+@pytest.mark.parametrize("example,k,kind", [(1, 1, "S"), (1, 1, "K"), (1, 1, "Kp"), (3, 1, "S")])
 def test_error_matches_paper(ggq, example, k, kind):
     surface, _, center, radius = EXAMPLES[example]
     Np, twoM, e_paper = printed(example)[k][kind]
+    op, rhs, rep = PROBLEMS[kind]
     Mt = twoM
     N = 16 * Np * Mt
-    A = ny.operator_rows(surface, Np, Mt, float(k), ggq[0], ggq[1], np.arange(N), op="S" if kind == "S" else "K-I")
-    x = np.linalg.solve(A, ny.point_source_rhs(surface, Np, Mt, float(k), SOURCE))
+    A = ny.operator_rows(surface, Np, Mt, float(k), ggq[0], ggq[1], np.arange(N), op=op)
+    x = np.linalg.solve(A, rhs(surface, Np, Mt, float(k), SOURCE))
     pts = ball_points(center, radius)
-    u = ny.field(surface, Np, Mt, float(k), x, pts, rep=kind)
+    u = ny.field(surface, Np, Mt, float(k), x, pts, rep=rep)
     ue = exact.point_source(float(k), pts, SOURCE)
     E = np.linalg.norm(u - ue) / len(ue)
     assert E <= 3 * e_paper, (E, e_paper)
