@@ -11,6 +11,11 @@ generators in ``workloads``):
       r = h(t, th) (sin t cos th, sin t sin th, cos t),
       h = 1 + sum_i c_i sin^p_i(t) cos^q_i(t) T_i(m_i th),
       T = cos if s_i == 0 else sin,  t in [0, pi]
+  {"kind": "bean"}
+      the bean of Section 5, Example 2 (given implicitly there): at height
+      z = cos t the surface is the ellipse x^2/A + (y + 0.3 cos(pi z))^2/B = 1 - z^2,
+      A = 0.64 (1 - 0.1 cos(pi z)), B = 0.64 (1 - 0.4 cos(pi z)), so
+      r = (sqrt(A) sin t cos th, -0.3 cos(pi z) + sqrt(B) sin t sin th, z),  t in [0, pi]
   {"kind": "torus", "a": a, "b": b, "c": c, "R": R, "eps": eps, "m": m}
       r = (a w cos t, b w sin t, c sin th),  w = R + cos th + eps cos(m t),
       t in [0, 2 pi] with r(0, th) = r(2 pi, th): a torus-like surface (the
@@ -117,6 +122,29 @@ def evaluate(surface, t, th):
         rtt = H(htt) * e + 2 * H(ht) * et + H(h) * ett
         rtth = H(htth) * e + H(ht) * eth + H(hth) * et + H(h) * etth
         rthth = H(hthth) * e + 2 * H(hth) * eth + H(h) * ethth
+        return r, rt, rth, rtt, rtth, rthth
+    if surface["kind"] == "bean":
+        # u = cos(pi z), z = cos t; p(t) = sqrt(A) sin t, q(t) = sqrt(B) sin t, y0(t) = -0.3 u
+        u = np.cos(np.pi * ct)
+        du = np.pi * st * np.sin(np.pi * ct)                            # d/dt cos(pi cos t)
+        ddu = np.pi * ct * np.sin(np.pi * ct) - (np.pi * st) ** 2 * u
+        def ellipse_factor(c0):
+            # f = 0.8 sqrt(1 - c0 u) sin t and its first two t-derivatives
+            g = 1 - c0 * u
+            sg = np.sqrt(g)
+            dg, ddg = -c0 * du, -c0 * ddu
+            dsg = dg / (2 * sg)
+            ddsg = ddg / (2 * sg) - dg * dg / (4 * g * sg)
+            return 0.8 * sg * st, 0.8 * (dsg * st + sg * ct), 0.8 * (ddsg * st + 2 * dsg * ct - sg * st)
+        pf, pt, ptt = ellipse_factor(0.1)
+        qf, qt, qtt = ellipse_factor(0.4)
+        y0, y0t, y0tt = -0.3 * u, -0.3 * du, -0.3 * ddu
+        r = np.stack([pf * cp, y0 + qf * sp, ct + z], -1)
+        rt = np.stack([pt * cp, y0t + qt * sp, -st + z], -1)
+        rth = np.stack([-pf * sp, qf * cp, z], -1)
+        rtt = np.stack([ptt * cp, y0tt + qtt * sp, -ct + z], -1)
+        rtth = np.stack([-pt * sp, qt * cp, z], -1)
+        rthth = np.stack([-pf * cp, -qf * sp, z], -1)
         return r, rt, rth, rtt, rtth, rthth
     if surface["kind"] == "torus":
         a, b, c = surface["a"], surface["b"], surface["c"]

@@ -209,3 +209,9 @@ def wiggly_torus():
     """The wiggly torus of the paper's Example 3: r = (1.2 w cos t, w sin t, 1.7 sin th),
     w = 2 + cos th + 0.25 cos 5t, t and th in [0, 2 pi) (t periodic)."""
     return {"kind": "torus", "a": 1.2, "b": 1.0, "c": 1.7, "R": 2.0, "eps": 0.25, "m": 5}
+
+
+def bean():
+    """The bean-shaped surface of the paper's Example 2 (given there implicitly; the oracle's geometry
+    parameterises it by z = cos t and the angle th around each horizontal elliptic cross-section)."""
+    return {"kind": "bean"}
