@@ -38,3 +38,28 @@ def test_parameter_count_matches_oracle():
     import oracle.precond as P
     m = re.search(r"#define\s+BIE_NET_PARAMS\s+(\d+)", open(HEADER).read())
     assert int(m.group(1)) == P.N_PARAMS
+
+
+def test_invalid_arguments_are_refused_before_any_device_call():
+    """Documented error behaviour of the boundary: a null handle or pointer gives BIE_EINVAL (1) and a
+    message naming the call, without touching the device (this runs on a machine without a GPU)."""
+    lib = ctypes.CDLL(LIB)
+    lib.bie_last_error.restype = ctypes.c_char_p
+    vp, d, i32, i64, u = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint
+    null = vp(None)
+    calls = {
+        "bie_surface_sample": (null, null, i32(4), i32(32), null, null),
+        "bie_kernel_modes": (null, null, u(1), d(1.0), null, null, i64(1), null),
+        "bie_assemble": (null, null, i32(0), d(1.0), d(1.0), null),
+        "bie_assemble_near": (null, null, u(1), d(1.0), d(1.0), d(0.0), d(0.0), d(0.0), null),
+        "bie_assemble_near_band": (null, null, u(1), d(1.0), d(1.0), d(0.0), d(0.0), d(0.0), null),
+        "bie_solve": (null, i64(4), null, null, i32(1), null, null, null),
+        "bie_field_eval": (null, null, i32(0), d(1.0), d(1.0), null, null, i64(1), i32(0), null),
+        "bie_blockdiag_create": (null, i64(64), null, i32(32), null),
+        "bie_batch_create": (null, i32(1), null, null, u(1), null, i64(1), null),
+    }
+    for name, args in calls.items():
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(*args) == 1, name
+        assert lib.bie_last_error().decode().startswith(name), (name, lib.bie_last_error())
