@@ -342,6 +342,83 @@ def _tau3_translated(H3, h3, a, b, A, Bn, M, H_a, H1_a):
 
 
 # ----------------------------------------------------------------------------
+# the O(M) route to <rho^{-1}>_l (Section 3.3, the "O(M) approach")
+# ----------------------------------------------------------------------------
+def rho_inv_modes_banded(surface, t, th, t_s, lmax, eps0=1e-14):
+    """<rho^{-1}>_l, l = 0..lmax, of one pair (t != t_s) from the difference equation Eq. (lin:diff).
+
+    Steps as the paper orders them:
+      1. <rho^2>_n by the trapezoid rule (rho^2 is analytic and periodic in th_s), and m0 by
+         Eq. (crt:M0), read as a bound on the whole tail: the smallest m0 with |<rho^2>_n| <=
+         eps0 max_k |<rho^2>_k| for every |n| > m0 (surfaces whose rho^2 skips some modes, like
+         the bumpy star, have isolated zero modes that the literal test at +-m0 alone would stop at);
+      2. the 2 m0 boundary values <rho^{-1}>_0..m0-1 and <rho^{-1}>_{lmax-m0+1}..lmax
+         (Eq. (offline:terms)) by quadrature (here the refined trapezoid of the definition);
+      3. a_j(i) = (m0 + 2i + j) <rho^2>_{m0-j} (Eq. (def:a_l)), i = 0..M1 = lmax - 2 m0, and the
+         banded system A x = b (Eq. (Axb)) for x = <rho^{-1}>_{m0}..<rho^{-1}>_{lmax-m0}, the
+         boundary values moved to b; A is Hermitian with band 2 m0 + 1 (Lemma after Eq. (root:x)).
+    Returns (modes [lmax+1], m0).
+    """
+    # 1. modes of rho^2 (a trigonometric polynomial of low degree on the surfaces used here; the grid
+    #    is refined until the modes stop changing)
+    n = 64
+    prev = None
+    while True:
+        thq = 2 * np.pi * np.arange(n) / n
+        near = _near_mask(t_s, thq, t, th)
+        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        c = np.fft.fft(np.sum(Y * Y, -1)) / n
+        if prev is not None and np.max(np.abs(c[:32] - prev[:32])) <= 1e-16 * np.max(np.abs(c)):
+            break
+        prev = np.concatenate([c[: n // 2], np.zeros(n // 2)])
+        n *= 2
+    rho2 = lambda k: c[k % n]
+    big = np.max(np.abs(c))
+    m0 = n // 4
+    while m0 > 1 and max(abs(rho2(m0)), abs(rho2(-m0))) <= eps0 * big:
+        m0 -= 1
+    # 2. boundary values by quadrature of the definition
+    M = lmax
+    R, _ = definition_rho_inv(surface, t, th, t_s, M)          # <rho^{-1}>_l, l = -M..M
+    out = np.zeros(lmax + 1, complex)
+    lo = list(range(0, m0))
+    hi = list(range(lmax - m0 + 1, lmax + 1))
+    for l in lo + hi:
+        out[l] = R[M + l]
+    # 3. the banded system: equation i couples <rho^{-1}>_{i..i+2 m0}
+    M1 = lmax - 2 * m0
+    A = np.zeros((M1 + 1, M1 + 1), complex)
+    b = np.zeros(M1 + 1, complex)
+    for i in range(M1 + 1):
+        for j in range(2 * m0 + 1):
+            a = (m0 + 2 * i + j) * rho2(m0 - j)
+            col = i + j - m0                                      # unknown x_col = <rho^{-1}>_{i+j}
+            if 0 <= col <= M1:
+                A[i, col] += a
+            else:
+                b[i] -= a * out[i + j]
+    out[m0:lmax - m0 + 1] = np.linalg.solve(A, b)
+    return out, m0
+
+
+def definition_rho_inv(surface, t, th, t_s, M, tol=1e-15, n_max=2 ** 22):
+    """<rho^{-1}>_m, m = -M..M, by the trapezoid rule refined until converged (plain definition)."""
+    n = max(8 * M, 64)
+    prev = None
+    while True:
+        thq = 2 * np.pi * np.arange(n) / n
+        near = _near_mask(t_s, thq, t, th)
+        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        c = np.fft.fft(1.0 / np.sqrt(np.sum(Y * Y, -1))) / n
+        m = np.arange(-M, M + 1)
+        cur = c[m % n]
+        if (prev is not None and np.max(np.abs(cur - prev)) <= tol * np.max(np.abs(cur))) or n >= n_max:
+            return cur, n
+        prev = cur
+        n *= 2
+
+
+# ----------------------------------------------------------------------------
 # the plain definition (brute force)
 # ----------------------------------------------------------------------------
 def definition_modes(surface, t, th, t_s, M, k, kernel="S", n_start=None, tol=1e-15, n_max=2 ** 22):

@@ -85,3 +85,18 @@ def test_far_root_is_capped():
     assert out["_b"][0] == km.B_CAP
     dS, _ = km.definition_modes(wl.sphere(), 0.0083, 0.0, 3.13, 8, 1.0, "S")
     assert _rel(out["S"][0], dS) <= 1e-13
+
+
+@pytest.mark.parametrize("surface,Mt", [(ELL, 64), (wl.bumpy(), 128)])
+@pytest.mark.parametrize("dt", [0.006, 0.05, 0.3])
+def test_banded_route_matches_swapped_route(surface, Mt, dt):
+    # two of the paper's routes to <rho^{-1}>_l: the O(M) difference equation Eq. (lin:diff) with
+    # quadrature boundary values, and singularity swapping Eq. (convolution); they share no step
+    # beyond the geometry
+    t, th = 1.1, 2 * np.pi * 5 / Mt
+    out = km.method_modes(surface, np.array([t]), np.array([th]), np.array([t + dt]), Mt, 1.0, ("S",),
+                          return_details=True)
+    R, rmax = out["_R"][0], out["_rmax"]
+    Rb, m0 = km.rho_inv_modes_banded(surface, t, th, t + dt, rmax)
+    assert m0 == (2 if surface is ELL else 10)   # rho^2 of the ellipsoid is a trig polynomial of degree 2
+    assert _rel(Rb, R[rmax:]) <= 1e-12
