@@ -9,6 +9,13 @@ factor FFT, singular convolution, Parseval weights) and the GGQ fill of the
 near blocks into the resident N x N matrix.  Inputs are resident in HBM; L2 is
 flushed (a 512 MiB write) before every timed step.
 
+Also reported on the same JSON line: the end-to-end rate (surface sampling from
+host descriptors and the near band [N][3][16 Mth] written to page-locked host
+memory through bie_assemble_near_band), the dominant pair-kernel launch against
+the measured FP64 rate (roofline), the single + double layer rate, the far fill,
+FGMRES iteration and field-evaluation figures (rows), the solves (FP64, mixed,
+learned preconditioner), and the batch scheduler.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 With --impl reference the oracle (plain FP64 numpy) is timed on bounded
