@@ -16,6 +16,10 @@ generators in ``workloads``):
       z = cos t the surface is the ellipse x^2/A + (y + 0.3 cos(pi z))^2/B = 1 - z^2,
       A = 0.64 (1 - 0.1 cos(pi z)), B = 0.64 (1 - 0.4 cos(pi z)), so
       r = (sqrt(A) sin t cos th, -0.3 cos(pi z) + sqrt(B) sin t sin th, z),  t in [0, pi]
+  {"kind": "fourier_torus", "R": R, "terms": [[c, m, n], ...]}
+      r = (w cos t, w sin t, zeta),  w = R + sum c cos(m th + n t),
+      zeta = sum c sin(m th + n t),  t in [0, 2 pi] periodic (the twisted torus
+      of Section 5, Example 4, has R = 4.5 and the six terms printed there)
   {"kind": "torus", "a": a, "b": b, "c": c, "R": R, "eps": eps, "m": m}
       r = (a w cos t, b w sin t, c sin th),  w = R + cos th + eps cos(m t),
       t in [0, 2 pi] with r(0, th) = r(2 pi, th): a torus-like surface (the
@@ -35,12 +39,12 @@ import numpy as np
 
 def parameter_length(surface):
     """Length L of the t-interval [0, L] (Section 2)."""
-    return 2 * np.pi if surface["kind"] == "torus" else np.pi
+    return 2 * np.pi if surface["kind"] in ("torus", "fourier_torus") else np.pi
 
 
 def is_periodic(surface):
     """Torus-like surface (r(0, th) = r(L, th)): the first and last panels are adjacent (Section 3.1)."""
-    return surface["kind"] == "torus"
+    return surface["kind"] in ("torus", "fourier_torus")
 
 
 def _sc_power(st, ct, p, q):
@@ -145,6 +149,32 @@ def evaluate(surface, t, th):
         rtt = np.stack([ptt * cp, y0tt + qtt * sp, -ct + z], -1)
         rtth = np.stack([-pt * sp, qt * cp, z], -1)
         rthth = np.stack([-pf * cp, -qf * sp, z], -1)
+        return r, rt, rth, rtt, rtth, rthth
+    if surface["kind"] == "fourier_torus":
+        w = surface["R"] + z
+        wt = z.copy(); wth = z.copy(); wtt = z.copy(); wtth = z.copy(); wthth = z.copy()
+        zt_ = z.copy(); zh = z.copy(); ztt = z.copy(); zth = z.copy(); zhh = z.copy(); zeta = z.copy()
+        for cc, m, n in surface["terms"]:
+            ph = m * th + n * t
+            cph, sph = np.cos(ph), np.sin(ph)
+            w = w + cc * cph
+            wt = wt - cc * n * sph
+            wth = wth - cc * m * sph
+            wtt = wtt - cc * n * n * cph
+            wtth = wtth - cc * m * n * cph
+            wthth = wthth - cc * m * m * cph
+            zeta = zeta + cc * sph
+            zt_ = zt_ + cc * n * cph
+            zh = zh + cc * m * cph
+            ztt = ztt - cc * n * n * sph
+            zth = zth - cc * m * n * sph
+            zhh = zhh - cc * m * m * sph
+        r = np.stack([w * ct, w * st, zeta], -1)
+        rt = np.stack([wt * ct - w * st, wt * st + w * ct, zt_], -1)
+        rth = np.stack([wth * ct, wth * st, zh], -1)
+        rtt = np.stack([wtt * ct - 2 * wt * st - w * ct, wtt * st + 2 * wt * ct - w * st, ztt], -1)
+        rtth = np.stack([wtth * ct - wth * st, wtth * st + wth * ct, zth], -1)
+        rthth = np.stack([wthth * ct, wthth * st, zhh], -1)
         return r, rt, rth, rtt, rtth, rthth
     if surface["kind"] == "torus":
         a, b, c = surface["a"], surface["b"], surface["c"]

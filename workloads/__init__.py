@@ -215,3 +215,10 @@ def bean():
     """The bean-shaped surface of the paper's Example 2 (given there implicitly; the oracle's geometry
     parameterises it by z = cos t and the angle th around each horizontal elliptic cross-section)."""
     return {"kind": "bean"}
+
+
+def twisted_torus():
+    """The twisted torus of the paper's Example 4, with the six terms as printed there (two of them,
+    cos th and -0.25 cos th, could be one term 0.75 cos th; kept as printed)."""
+    return {"kind": "fourier_torus", "R": 4.5,
+            "terms": [[0.17, 2, -1], [0.11, 2, 0], [1.0, 1, 0], [-0.25, 1, 0], [0.01, 1, 1], [-0.45, -1, 1]]}
