@@ -179,12 +179,18 @@ def _pair_samples(surface, t, th, t_s, Mt):
     return thq, T_s, TH_s, T, TH, near, Y
 
 
-def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=False):
+def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=False, f_rule=False):
     """Kernel modes by singularity swapping; dict kernel -> (B, Mt+1) complex (m = -M..M).
 
     Also returns, per kernel, the swapped part "<kernel>_sing" (modes) and the
     smooth part "<kernel>_smooth" (its samples on the theta grid: i sin(k rho)/rho
     for S, -i beta tau_0 for K), whose Parseval weights are the trapezoid rule.
+
+    By default F keeps the Mth modes of its grid samples (p = M, the reading the library's kernels
+    follow).  With f_rule, p follows the paper's rule for the expansion of F (Eq. (F-expansion) with a
+    criterion like Eq. (crt:M0)): F is sampled on grids of 2, 4, ... times Mth points until its modes
+    at |j| >= p - 1 fall below 1e-14 of the largest, for surfaces where other complex roots of rho^2
+    lie near the real axis and F needs more than Mth modes.
     """
     t = np.atleast_1d(np.asarray(t, float))
     th = np.atleast_1d(np.asarray(th, float))
@@ -201,9 +207,25 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
     f = sym_modes(F, M)
     need_k = "K" in kernels or "Kp" in kernels
     L = (4 if need_k else 3) * M
+    rmax = 3 * M if need_k else 2 * M
+    if f_rule:
+        p, qq = M, 1
+        while qq < 16:
+            tail = np.max(np.abs(np.concatenate([f[:, :2], f[:, -2:]], axis=1)), axis=1)
+            if np.all(tail <= 1e-14 * np.max(np.abs(f), axis=1)):
+                break
+            qq *= 2
+            n = qq * Mt
+            thf = 2 * np.pi * np.arange(n) / n
+            Tsf, THsf = np.broadcast_to(t_s[:, None], (len(t), n)), np.broadcast_to(thf[None, :], (len(t), n))
+            Tf, THf = np.broadcast_to(t[:, None], (len(t), n)), np.broadcast_to(th[:, None], (len(t), n))
+            Yf = geo.difference(surface, Tsf, THsf, Tf, THf, _near_mask(Tsf, THsf, Tf, THf))
+            sf = (-np.expm1(-b))[:, None] ** 2 + 4 * q[:, None] * np.sin((thf[None, :] - a[:, None]) / 2) ** 2
+            p = qq * M
+            f = sym_modes(np.sqrt(sf / np.sum(Yf * Yf, -1)), p)
+        L = max(L, rmax + p + 1)
     A, D = sp.a_modes(b, L)
     out = {}
-    rmax = 3 * M if need_k else 2 * M
     R = swap_convolution(f, a, A, rmax)                                        # <rho^{-1}>_l
     if "S" in kernels:
         C = sym_modes(np.cos(k * rho), M)

@@ -110,7 +110,7 @@ def near_pairs(Np, Mt, rows, ggq_x, L=np.pi, periodic=False):
     return out
 
 
-def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=None):
+def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=None, f_rule=False):
     """Dense rows of the S and/or K matrices: dict kind -> (len(rows), N).  Near pairs go through
     the per-pair pipeline in batches of `chunk` (default: about 200 MB of convolution table)."""
     if chunk is None:
@@ -154,7 +154,7 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=No
         ip = (r // (16 * Mt) + di - 1) % Np
         pos = np.array([row_pos[v] for v in r])
         cols = ip[:, None, None] * 16 * Mt + np.arange(16)[None, :, None] * Mt + np.arange(Mt)[None, None, :]
-        modes = km.method_modes(surface, t, tht, ts, Mt, k, kernels=tuple(kinds))
+        modes = km.method_modes(surface, t, tht, ts, Mt, k, kernels=tuple(kinds), f_rule=f_rule)
         for kd in kinds:
             W = parseval_weights_split(modes[kd + "_sing"], modes[kd + "_smooth"])
             vals = coef[di, l, g][:, :, None] * W[:, None, :]
@@ -162,11 +162,11 @@ def assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds=("S",), chunk=No
     return out
 
 
-def operator_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, op="S", eta=None):
-    """Rows of the operator matrix acting on the weighted density."""
+def operator_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, op="S", eta=None, f_rule=False):
+    """Rows of the operator matrix acting on the weighted density (f_rule: see method_modes)."""
     kinds = {"S": ("S",), "K": ("K",), "K+I": ("K",), "K-I": ("K",), "CFIE": ("S", "K"),
              "Kp": ("Kp",), "Kp+I": ("Kp",), "Kp-I": ("Kp",)}[op]
-    blocks = assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds)
+    blocks = assemble_rows(surface, Np, Mt, k, ggq_x, ggq_w, rows, kinds, f_rule=f_rule)
     if op == "S":
         return blocks["S"]
     A = blocks[kinds[0] if op.startswith("Kp") else "K"]

@@ -100,3 +100,17 @@ def test_banded_route_matches_swapped_route(surface, Mt, dt):
     Rb, m0 = km.rho_inv_modes_banded(surface, t, th, t + dt, rmax)
     assert m0 == (2 if surface is ELL else 10)   # rho^2 of the ellipsoid is a trig polynomial of degree 2
     assert _rel(Rb, R[rmax:]) <= 1e-12
+
+
+@pytest.mark.parametrize("t,th,ts", [(4.186, 1.571, 4.213), (3.651, 1.508, 3.647), (2.518, 4.650, 2.531)])
+def test_paper_p_rule_on_the_twisted_torus(t, th, ts):
+    # On the twisted torus of Example 4 other complex roots of rho^2 come close to the real axis for
+    # some pairs, and F needs more than Mth modes: with p = M these pairs are off by 2e-11..6e-11 at
+    # Mth = 100; the paper's rule for p (Eq. (F-expansion), a criterion like Eq. (crt:M0)) recovers
+    # the definition to rounding.
+    S = wl.twisted_torus()
+    d, _ = km.definition_modes(S, t, th, ts, 50, 1.0, "S")
+    plain = km.method_modes(S, np.array([t]), np.array([th]), np.array([ts]), 100, 1.0, ("S",))
+    rule = km.method_modes(S, np.array([t]), np.array([th]), np.array([ts]), 100, 1.0, ("S",), f_rule=True)
+    assert _rel(plain["S"][0], d) > 1e-11
+    assert _rel(rule["S"][0], d) <= 1e-13
