@@ -17,6 +17,13 @@
  *  - Errors are reported by the return value (bie_status); bie_last_error()
  *    returns a thread-local description of the last failure.  No entry point
  *    aborts, traps or falls back to the CPU: there is no CPU path.
+ *  - A context (bie_ctx) owns the pair pipeline's work buffers (grown on
+ *    demand, freed by bie_ctx_free); calls on one context are ordered by its
+ *    stream, and calls on different contexts (other streams, other host
+ *    threads) may run concurrently.  The recurrence coefficient table is one
+ *    read-only array per device, allocated on first use and kept until exit.
+ *    Every call that launches work checks that the context's device is the
+ *    current device (BIE_EINVAL otherwise).
  *  - Index of an unknown / collocation node: (panel*16 + node)*Mth + l, with
  *    panel = 0..Np-1 (uniform panels of [0, L]), node = 0..15 (Gauss-Legendre),
  *    l = 0..Mth-1 (theta_l = 2 pi l / Mth).  The unknown is the weighted
@@ -103,7 +110,8 @@ typedef struct {
  * normals, Jacobians and the data the pair pipeline needs (Section 2 and the
  * Section 4 Remark on second derivatives).  Allocates device memory owned by
  * the returned handle.  Np in [2, 4096]; Mth even, in [8, 1024], of the form
- * 2^a 3^b.  Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.                      */
+ * 2^a 3^b.  Errors: BIE_EINVAL, BIE_ENAN (a NaN or Inf in the descriptor or
+ * the tables), BIE_ENOMEM, BIE_ECUDA.                                       */
 bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int n_panels,
                               int m_theta, const bie_quad_tables* ggq, bie_surface* out);
 void bie_surface_free(bie_surface s);
@@ -154,7 +162,8 @@ bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kernels, double
  *   The first call on a device takes the device addresses of the arrays and
  *   copies the recurrence coefficients into them (cudaGetSymbolAddress,
  *   cudaMemcpyToSymbol) with that device current; make that first call before
- *   any stream capture.
+ *   any stream capture.  Every call checks that the context's device is the
+ *   current device (BIE_EINVAL otherwise), since the addresses are per device.
  *   All calls share the arrays: calls that may overlap on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller.
  *   Nothing in the arrays needs clearing between calls: every table entry is

@@ -21,6 +21,17 @@ bie_status cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? BIE_ENOMEM : BIE_ECUDA;
 }
 
+bie_status check_device(bie_ctx ctx, const char* where) {
+  int cur = -1;
+  const cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  if (cur != ctx->device) {
+    set_error("%s: the context's device (%d) is not the current device (%d)", where, ctx->device, cur);
+    return BIE_EINVAL;
+  }
+  return BIE_OK;
+}
+
 }  // namespace bie
 
 extern "C" {
@@ -48,6 +59,9 @@ bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream) {
 
 void bie_ctx_free(bie_ctx ctx) {
   if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->pair_scratch);
+  cudaFree(ctx->pair_records);
   cudaFree(ctx->d_status);
   delete ctx;
 }

@@ -316,6 +316,12 @@ struct bie_ctx_s {
   int device;
   int sms;
   int* d_status;       // device status word (error flags from kernels)
+  // pair-pipeline work buffers of this context (grown on demand, freed by bie_ctx_free): the
+  // per-warp recurrence scratch of the fused kernels and the per-pair records of the split launch
+  double* pair_scratch = nullptr;
+  size_t pair_scratch_bytes = 0;
+  double* pair_records = nullptr;
+  size_t pair_records_bytes = 0;
 };
 
 struct bie_surface_s {
@@ -348,6 +354,8 @@ struct bie_net_infer_s;
 namespace bie {
 void set_error(const char* fmt, ...);
 bie_status cuda_fail(cudaError_t e, const char* where);
+// BIE_OK if the context's device is the current one, else BIE_EINVAL naming the call
+bie_status check_device(bie_ctx ctx, const char* where);
 // preconditioners (blockdiag.cu, precond_net.cu)
 bie_status blockdiag_apply_dev(bie_blockdiag P, const double2* r, int nv, double2* z);
 bie_status blockdiag_apply_f32(bie_blockdiag P, const float2* r, int nv, float2* z);

@@ -30,6 +30,7 @@
 //      -i beta tau_0) by the trapezoid rule (Section 3.2).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "bie_internal.cuh"
@@ -1136,15 +1137,26 @@ static std::vector<double> recurrence_table(int n) {
   return r;
 }
 
-struct PairResources {
-  double* rec = nullptr;
-  int rec_len = 0;
-  double* scratch = nullptr;
-  size_t scratch_bytes = 0;
-  double* records = nullptr;   // split launch: per-pair records of one chunk
-  size_t records_bytes = 0;
-};
-static PairResources g_res;   // grown on demand (the library drives one device per process)
+// Recurrence coefficient table, one per device, allocated once at the size the largest grid of the
+// library needs (Mth <= 1024: L <= 2048) and never freed, so that plans and captured graphs holding
+// its address stay valid for the life of the process.
+constexpr int kMaxMtLib = 1024;
+constexpr int kRecLenMax = (int)(3.8 * 2 * kMaxMtLib) + 64;   // Miller needs N < 3.8 L + 17 (it runs only when L b > 7)
+static double* g_rec[64];
+static std::mutex g_rec_mu;
+
+// grow a context-owned device buffer (stream-synchronised free of the old one)
+static bie_status grow(bie_ctx ctx, double** buf, size_t* have, size_t need, const char* what) {
+  if (*have >= need) return BIE_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  const cudaError_t e = cudaMalloc((void**)buf, need);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  *have = need;
+  return BIE_OK;
+}
 
 PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   PairArgs a = {};
@@ -1191,19 +1203,24 @@ int pair_warps_per_block(int Mt, unsigned kernels) {
   return best;
 }
 
-static bie_status ensure_rec(cudaStream_t stream, int L) {
-  const int need_rec = (int)(3.8 * L) + 64;   // Miller needs N < 3.8 L + 17 (it runs only when L b > 7)
-  if (g_res.rec_len >= need_rec) return BIE_OK;
-  std::vector<double> r = recurrence_table(need_rec);
-  cudaStreamSynchronize(stream);
-  if (g_res.rec) cudaFree(g_res.rec);
-  g_res.rec = nullptr;
-  g_res.rec_len = 0;
-  cudaError_t e = cudaMalloc((void**)&g_res.rec, sizeof(double) * r.size());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(recurrence table)");
-  e = cudaMemcpy(g_res.rec, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(recurrence table)");
-  g_res.rec_len = need_rec;
+static bie_status ensure_rec(bie_ctx ctx, int L, const double** rec, int* rec_len) {
+  if (L < 0 || L > 2 * kMaxMtLib) { set_error("recurrence table: L = %d beyond the library limit", L); return BIE_EINVAL; }
+  const bie_status ds = check_device(ctx, "pair pipeline");
+  if (ds != BIE_OK) return ds;
+  if (ctx->device < 0 || ctx->device >= 64) { set_error("pair pipeline: device ordinal out of range"); return BIE_EINVAL; }
+  std::lock_guard<std::mutex> lock(g_rec_mu);
+  double*& t = g_rec[ctx->device];
+  if (!t) {
+    const std::vector<double> r = recurrence_table(kRecLenMax);
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, sizeof(double) * r.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(recurrence table)");
+    e = cudaMemcpy(d, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cudaMemcpy(recurrence table)"); }
+    t = d;
+  }
+  *rec = t;
+  *rec_len = kRecLenMax;
   return BIE_OK;
 }
 
@@ -1212,26 +1229,18 @@ constexpr int64_t kSplitChunk = 1 << 20;
 
 static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
   const cudaStream_t st = s->ctx->stream;
-  bie_status rs = ensure_rec(st, a.L);
+  bie_status rs = ensure_rec(s->ctx, a.L, &a.rec, &a.rec_len);
   if (rs != BIE_OK) return rs;
-  a.rec = g_res.rec;
-  a.rec_len = g_res.rec_len;
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(a.n_pairs, kSplitChunk));
   const int64_t per_pair = 8 + 2 * 33 + (a.L + 1) + a.Mt;
   const size_t rbytes = sizeof(double) * (size_t)(per_pair * chunk);
   cudaError_t e;
-  if (g_res.records_bytes < rbytes) {
-    cudaStreamSynchronize(st);
-    if (g_res.records) cudaFree(g_res.records);
-    g_res.records = nullptr;
-    g_res.records_bytes = 0;
-    e = cudaMalloc((void**)&g_res.records, rbytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pair records)");
-    g_res.records_bytes = rbytes;
-  }
-  a.rec_hdr = g_res.records;
-  a.rec_E = reinterpret_cast<float4*>(g_res.records + 8 * chunk);
-  a.rec_A = g_res.records + (8 + 2 * 33) * chunk;
+  rs = grow(s->ctx, &s->ctx->pair_records, &s->ctx->pair_records_bytes, rbytes, "cudaMalloc(pair records)");
+  if (rs != BIE_OK) return rs;
+  double* records = s->ctx->pair_records;
+  a.rec_hdr = records;
+  a.rec_E = reinterpret_cast<float4*>(records + 8 * chunk);
+  a.rec_A = records + (8 + 2 * 33) * chunk;
   a.rec_R2 = a.rec_A + (a.L + 1) * chunk;
   // root kernel: register-limited occupancy, no shared memory
   int per_r = 0;
@@ -1285,23 +1294,17 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   {
-    const bie_status rs = ensure_rec(s->ctx->stream, a.L);
+    const bie_status rs = ensure_rec(s->ctx, a.L, &a.rec, &a.rec_len);
     if (rs != BIE_OK) return rs;
   }
   a.scratch_per_warp = pair_scratch_per_warp(a.L, withK, a.Mt);
   const size_t sbytes = sizeof(double) * (size_t)a.scratch_per_warp * (size_t)blocks * wpb;
-  if (g_res.scratch_bytes < sbytes) {
-    cudaStreamSynchronize(s->ctx->stream);
-    if (g_res.scratch) cudaFree(g_res.scratch);
-    g_res.scratch = nullptr;
-    g_res.scratch_bytes = 0;
-    e = cudaMalloc((void**)&g_res.scratch, sbytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pair scratch)");
-    g_res.scratch_bytes = sbytes;
+  {
+    const bie_status rs = grow(s->ctx, &s->ctx->pair_scratch, &s->ctx->pair_scratch_bytes, sbytes,
+                               "cudaMalloc(pair scratch)");
+    if (rs != BIE_OK) return rs;
   }
-  a.rec = g_res.rec;
-  a.rec_len = g_res.rec_len;
-  a.scratch = g_res.scratch;
+  a.scratch = s->ctx->pair_scratch;
   kern<<<(unsigned)blocks, 32 * wpb, smem, s->ctx->stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch");
@@ -1376,18 +1379,16 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
   }
   if (ctx->device < 0 || ctx->device >= 64) { set_error("bie_kernel_modes_noalloc: device ordinal out of range"); return BIE_EINVAL; }
   if (n_pairs == 0) return BIE_OK;
+  // every call: the symbol addresses below belong to the context's device, so it must be current
+  {
+    const bie_status ds = check_device(ctx, "bie_kernel_modes_noalloc");
+    if (ds != BIE_OK) return ds;
+  }
   NoAllocState& st = g_noalloc[ctx->device];
   if (!st.ready) {
     // once per device, with that device current: device addresses of the static arrays and the
     // recurrence coefficients (a copy into the static table, no allocation)
-    int cur = -1;
-    cudaError_t e = cudaGetDevice(&cur);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (cur != ctx->device) {
-      set_error("bie_kernel_modes_noalloc: the context's device (%d) is not current (%d)", ctx->device, cur);
-      return BIE_EINVAL;
-    }
-    e = cudaGetSymbolAddress((void**)&st.scratch, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress((void**)&st.scratch, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
     e = cudaGetSymbolAddress((void**)&st.rec, g_noalloc_rec);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(recurrence table)");
@@ -1564,11 +1565,13 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
   }
   (void)nk;
   b->total_pairs = off;
-  bie_status st = ensure_rec(ctx->stream, (b->withK ? 4 : 3) * (b->maxMt / 2));
+  const double* rec = nullptr;
+  int rec_len = 0;
+  bie_status st = ensure_rec(ctx, (b->withK ? 4 : 3) * (b->maxMt / 2), &rec, &rec_len);
   if (st != BIE_OK) { delete b; return st; }
   for (auto& a : b->host_args) {
-    a.rec = g_res.rec;
-    a.rec_len = g_res.rec_len;
+    a.rec = rec;
+    a.rec_len = rec_len;
   }
   cudaError_t e = cudaMalloc((void**)&b->d_args, sizeof(PairArgs) * n_surf);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));

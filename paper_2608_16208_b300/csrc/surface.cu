@@ -68,6 +68,21 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
     set_error("bie_surface_sample: n_terms %d out of [0, %d]", desc->n_terms, BIE_MAX_TERMS);
     return BIE_EINVAL;
   }
+  {
+    // non-finite descriptor values or tables would sample NaN geometry: refuse them here
+    bool finite = true;
+    if (desc->kind == 0)
+      for (int c = 0; c < 3; ++c) finite = finite && std::isfinite(desc->axes[c]);
+    else
+      for (int i = 0; i < 5 * desc->n_terms; ++i) finite = finite && std::isfinite(desc->terms[i]);
+    for (int i = 0; i < 3 * 16 * 16; ++i)
+      finite = finite && std::isfinite((&ggq->x[0][0][0])[i]) && std::isfinite((&ggq->w[0][0][0])[i]);
+    if (!finite) { set_error("bie_surface_sample: NaN or Inf in the surface descriptor or the quadrature tables"); return BIE_ENAN; }
+  }
+  {
+    const bie_status ds = check_device(ctx, "bie_surface_sample");
+    if (ds != BIE_OK) return ds;
+  }
   bie_surface s = new bie_surface_s();
   memset(&s->sp, 0, sizeof(s->sp));
   s->ctx = ctx;

@@ -1,0 +1,95 @@
+"""GPU parity at the large theta grids the batch workload uses (Mth = 192 and 256: transform lengths
+P = 576..1024, the largest shared-memory carve of the pair kernels) and for a batch that mixes every
+grid size of that workload (Mth in {64, 96, 128, 192, 256}) in one persistent launch.
+
+Per pair, normwise: max_m |gpu - oracle| / max_m |oracle| <= 1e-12 against the FP64 oracle's method
+mode (Section 3.3, Eqs. (F-smooth), (Am), (convolution); Section 4, Eqs. (dis:K), (tau1),
+(tau3-standard), (tau3-modified))."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import kernel_modes as km
+from oracle import nystrom as ny
+from tests.pairs import pair_geometry, sample_pairs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bie():
+    import paper_2608_16208_b300 as b
+    return b
+
+
+@pytest.fixture(scope="module")
+def ctx(bie):
+    return bie.Context()
+
+
+@pytest.mark.parametrize("Mt", [192, 256])
+@pytest.mark.parametrize("kernels", [("S",), ("S", "K")])
+def test_modes_large_grids(bie, ctx, ggq, Mt, kernels):
+    surface, Np, k = wl.harmonic_star(0, 300, 0.12), 8, 12.0
+    s = bie.Surface(ctx, surface, Np, Mt, ggq)
+    rows, srcs = sample_pairs(Np, Mt, 300, seed=6)
+    mask = bie.KERNEL_S | (bie.KERNEL_K if "K" in kernels else 0)
+    out = bie.kernel_modes(s, mask, k, torch.from_numpy(rows).cuda(), torch.from_numpy(srcs).cuda())
+    ctx.sync()
+    t, th, ts = pair_geometry(Np, Mt, rows, srcs, ggq[0])
+    chunks = [km.method_modes(surface, t[c:c + 128], th[c:c + 128], ts[c:c + 128], Mt, k, kernels)
+              for c in range(0, len(t), 128)]
+    for idx, kd in enumerate(kernels):
+        got = out[:, idx, :].cpu().numpy()
+        ref = np.concatenate([ch[kd] for ch in chunks])
+        assert np.all(np.isfinite(got))
+        err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+        assert err.max() <= TOL, "%s Mth=%d: worst pair %d: %.3e" % (kd, Mt, err.argmax(), err.max())
+
+
+def _decode(p, Mt):
+    i = p % Mt
+    rest = p // Mt
+    g = rest % 16
+    rest //= 16
+    d = rest % 3
+    tn = rest // 3
+    return tn * Mt + i, d * 16 + g
+
+
+@pytest.mark.parametrize("kernels", [("S",), ("S", "K")])
+def test_batch_every_grid_size(bie, ggq, kernels):
+    """One persistent launch over five harmonic stars with Mth = 64, 96, 128, 192, 256 (ordered largest
+    first by the plan); sampled pairs of every surface against the oracle's Parseval weights."""
+    ctx = bie.Context()
+    specs = [(wl.harmonic_star(0, 310 + i, 0.15 * (i + 1) / 5), Np, Mt, k)
+             for i, (Np, Mt, k) in enumerate([(3, 64, 17.0), (2, 96, 4.0), (3, 128, 11.0), (2, 192, 8.5),
+                                              (2, 256, 19.0)])]
+    surfs = [bie.Surface(ctx, sp, Np, Mt, ggq) for sp, Np, Mt, _ in specs]
+    total = sum(16 * Np * 48 * Mt for _, Np, Mt, _ in specs)
+    maxMt = max(Mt for _, _, Mt, _ in specs)
+    nk = len(kernels)
+    mask = bie.KERNEL_S | (bie.KERNEL_K if "K" in kernels else 0)
+    W = torch.full((nk, total, maxMt), complex("nan"), dtype=torch.complex128, device="cuda")
+    b = bie.Batch(ctx, surfs, [k for *_, k in specs], mask, W, total)
+    assert b.pairs == total
+    b.run()
+    ctx.sync()
+    rs = wl.Stream(5, 2)
+    for sidx, (sp, Np, Mt, k) in enumerate(specs):
+        n_enum = 16 * Np * 48 * Mt
+        ps = np.unique(rs.integers(0, n_enum - 1, 90))
+        rows, srcs = (np.array(v) for v in zip(*[_decode(p, Mt) for p in ps]))
+        ip = rows // (16 * Mt) + srcs // 16 - 1
+        ok = (ip >= 0) & (ip < Np)
+        idx = torch.from_numpy(b.offsets[sidx] + ps).cuda()
+        t, th, ts = pair_geometry(Np, Mt, rows[ok], srcs[ok], ggq[0])
+        o = km.method_modes(sp, t, th, ts, Mt, k, kernels)
+        for kk, kd in enumerate(kernels):
+            got = W[kk, idx, :Mt].cpu().numpy()
+            assert np.all(got[~ok] == 0)
+            ref = ny.parseval_weights_split(o[kd + "_sing"], o[kd + "_smooth"])
+            err = np.max(np.abs(got[ok] - ref), axis=1) / np.max(np.abs(ref), axis=1)
+            assert err.max() <= TOL, (sidx, kd, Mt, err.max())

@@ -74,6 +74,28 @@ def test_mixed_precision_solve_reaches_tolerance(bie, ctx, ggq):
         assert np.linalg.norm(u - ue) / np.linalg.norm(ue) <= 1e-6
 
 
+@pytest.mark.parametrize("op", ["S", "CFIE"])
+def test_mixed_solve_fields_match_fp64_solve(bie, ctx, ggq, op):
+    """The mixed solve (FP32 storage inside FGMRES, FP64 refinement) against the FP64 GPU solve of the
+    same system: scattered fields at exterior points and far-field directions agree to 1e-8 relative."""
+    k, d = 4.0, [0.3, -0.2, 0.93]
+    surf = wl.ellipsoid(1.0, 0.8, 0.6)
+    s = bie.Surface(ctx, surf, 6, 48, ggq)
+    flag = bie.OP_S if op == "S" else bie.OP_CFIE | bie.UNWEIGHTED
+    A = bie.assemble(s, flag, k)
+    g = bie.rhs(s, 0, d, k)
+    tol = 1e-10
+    x64, r64 = bie.solve(ctx, A, g, tol=tol, restart=300, maxit=3000, prec=0)
+    x32, r32 = bie.solve(ctx, A, g, tol=tol, restart=300, maxit=3000, prec=1)
+    assert r64["rel_residual"] <= tol and r32["rel_residual"] <= tol and r32["refinements"] >= 1
+    pts = wl.exterior_points(16, 3.0)
+    dirs = wl.Stream(0, 9).directions(32)
+    for where, far in ((pts, False), (dirs, True)):
+        u64 = bie.field_eval(s, flag, k, x64, where, far_field=far).cpu().numpy()
+        u32 = bie.field_eval(s, flag, k, x32, where, far_field=far).cpu().numpy()
+        assert np.linalg.norm(u32 - u64) / np.linalg.norm(u64) <= 1e-8, (op, far)
+
+
 def test_cfie_exterior_point_source(bie, ctx, ggq):
     # exterior Dirichlet problem through the combined-field operator I + K - i k S
     k, src = 4.0, [0.1, 0.1, -0.05]

@@ -19,8 +19,10 @@ TOL = 1e-12
 def test_noalloc_matches_kernel_modes_twice(ggq):
     import paper_2608_16208_b300 as bie
     ctx = bie.Context()
+    # the last case fills the static scratch: Mth = 128 with the double layer (L = 256)
     for surface, Np, Mt, k, kern in [(wl.ellipsoid(1.0, 0.8, 0.6), 16, 128, 10.0, bie.KERNEL_S),
-                                      (wl.bumpy(), 6, 96, 5.0, bie.KERNEL_S | bie.KERNEL_K)]:
+                                      (wl.bumpy(), 6, 96, 5.0, bie.KERNEL_S | bie.KERNEL_K),
+                                      (wl.bumpy(), 8, 128, 20.0, bie.KERNEL_S | bie.KERNEL_K)]:
         s = bie.Surface(ctx, surface, Np, Mt, ggq)
         rows, srcs = sample_pairs(Np, Mt, 3000, seed=4)
         r = torch.from_numpy(rows).cuda()
