@@ -74,7 +74,9 @@ typedef enum {
 bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream);
 void bie_ctx_free(bie_ctx ctx);
 const char* bie_last_error(void);
-/* Wait for all work of the context's stream; returns BIE_ECUDA on a device error. */
+/* Wait for all work of the context's stream; returns BIE_ECUDA on a device error,
+ * BIE_EINVAL if a kernel met an invalid pair, BIE_ETIMEOUT if a bounded device
+ * wait expired (both flags are cleared by the call). */
 bie_status bie_ctx_sync(bie_ctx ctx);
 
 /* ---- surfaces (Section 2, Eq. (para); Section 3.1) -------------------------
@@ -321,21 +323,57 @@ bie_status bie_net_precond_apply(bie_net net, bie_blockdiag block, bie_surface s
                                  const double* v, int nv, double* z);
 
 /* ---- dense solve -------------------------------------------------------------
- * Restarted FGMRES (right preconditioned, classical Gram-Schmidt with
- * re-orthogonalisation) on A x = b for nrhs right-hand sides, one after the
- * other, until ||b - A x|| <= tol ||b||.
- *   A    [dev] double2[N][N] row-major;  rhs [dev] double2[nrhs][N];
- *   x    [dev] double2[nrhs][N] (initial guess in, solution out).
- *   prec 0 = FP64 matvec, 1 = FP32-stored matrix inside FGMRES with FP64
- *        iterative refinement (outer residuals in FP64).
- *   precond 0 = none; 1 = block-diagonal (block); 2 = learned (net on the
- *        grid of surface, wavenumber k, on top of block if it is not NULL).
- *        With precond = 2 a solve that does not converge or meets a NaN is
- *        run again with precond = 1 from the initial guess (fallback_used).
- * Uses device work memory of (2 restart + 4) N double2 (+ N*N float2 for
- * prec = 1), allocated stream-ordered and freed before return.
- * report[host] (may be NULL): iterations, final relative residual, flags.
- * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ENOCONV, BIE_ENAN, BIE_ECUDA.           */
+ * The paper states the system (Section 3.4) and no solver; this one is restarted
+ * FGMRES (right preconditioned, classical Gram-Schmidt with re-orthogonalisation)
+ * run for up to 16 right-hand sides in lockstep: every iteration makes one pass
+ * over the matrix for all of them (a block product), until
+ * ||b - A x|| <= tol ||b|| for each.
+ *
+ * bie_matrix: an assembled system matrix and the low-precision copies the mixed
+ * solves read.  The FP64 matrix A [dev] double2[n][n] (row-major) stays
+ * caller-owned and must outlive the handle; store (bit mask) adds copies owned by
+ * the handle: BIE_STORE_FP32 (FP32 complex, 8 n^2 bytes) and BIE_STORE_BF16X2
+ * (split BF16: hi = bf16(a), lo = bf16(a - hi) for every real component, 8 n^2
+ * bytes plus padding of rows to 128 and columns to 32, laid out in the tensor
+ * cores' shared-memory image).  Made once per matrix, it serves any number of
+ * solves.  Asynchronous on the ctx stream.  Errors: BIE_EINVAL, BIE_ENOMEM,
+ * BIE_ECUDA.
+ * bie_matrix_matvec: y [nr][n] = A x [nr][n] (both [dev] double2, 1 <= nr <= 16)
+ * with the product prec: 0 FP64 arithmetic; 1 the FP32 copy (FP32 products,
+ * chunk sums in FP64); 2 the split-BF16 copy on the tensor cores (tcgen05,
+ * FP32 accumulation, accumulators added in FP64; relative error about 1e-5);
+ * 3 FP64 storage with double-word products (about 2^-44; the refinement
+ * residual of the mixed solves).  Errors: BIE_EINVAL (a copy the product needs
+ * is missing), BIE_ECUDA; a bounded wait that expired inside the tensor-core
+ * product is reported by the next bie_solve as BIE_ETIMEOUT.                    */
+#define BIE_STORE_FP32 1u
+#define BIE_STORE_BF16X2 2u
+bie_status bie_matrix_create(bie_ctx ctx, int64_t n, const double* A, unsigned store, bie_matrix* out);
+void bie_matrix_free(bie_matrix M);
+int64_t bie_matrix_size(bie_matrix M);
+bie_status bie_matrix_matvec(bie_matrix M, int prec, const double* x, int nr, double* y);
+
+/* bie_solve_matrix: solve A x = b for nrhs right-hand sides (blocks of up to 16).
+ *   rhs [dev] double2[nrhs][n];  x [dev] double2[nrhs][n] (initial guess in,
+ *   solution out).
+ *   prec 0 = FP64 products throughout; 1 = FP32 products inside FGMRES, 2 =
+ *        split-BF16 tensor-core products inside FGMRES, each with FP64-accurate
+ *        iterative refinement outside (residuals b - A x by product 3, x += dx);
+ *        prec 1 and 2 need the matching copy in the bie_matrix.
+ *   precond 0 = none; 1 = block-diagonal (block); 2 = learned (net on the grid of
+ *        surface, wavenumber k, on top of block if it is not NULL).  With
+ *        precond = 2 a block that does not converge or meets a NaN is run again
+ *        with precond = 1 from the initial guess (fallback_used).
+ * Uses device work memory of about (2 restart + 6) n double2 per right-hand side
+ * of a block, allocated stream-ordered and freed before return; synchronises
+ * the ctx stream.
+ * report[host] (may be NULL): iterations (block iterations, summed over blocks and
+ * refinements), final relative residual (max over right-hand sides, from an
+ * FP64-accurate product), refinements, fallback, wall time, matrix products.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ENOCONV, BIE_ENAN (NaN or Inf in the data
+ * or the iterates), BIE_ETIMEOUT, BIE_ECUDA.
+ * bie_solve: the same for a bare FP64 matrix A [dev] double2[n][n]; it makes the
+ * copy prec needs for the duration of the call.                                 */
 typedef struct {
   double tol;
   int restart;
@@ -348,12 +386,15 @@ typedef struct {
   double k;              /* precond 2: wavenumber feature */
 } bie_solve_opts;
 typedef struct {
-  int iterations;        /* total inner iterations over all right-hand sides */
-  int refinements;       /* outer FP64 refinement steps (prec = 1)            */
-  double rel_residual;   /* max over right-hand sides, FP64 residual          */
-  double seconds;        /* wall time of the call                             */
-  int fallback_used;     /* precond = 2 fell back to the block preconditioner */
+  int iterations;        /* block iterations (one block product each)          */
+  int refinements;       /* outer FP64-accurate refinement steps (prec 1, 2)    */
+  double rel_residual;   /* max over right-hand sides                           */
+  double seconds;        /* wall time of the call                               */
+  int fallback_used;     /* precond = 2 fell back to the block preconditioner   */
+  int matvecs;           /* block products with the matrix (all precisions)     */
 } bie_solve_report;
+bie_status bie_solve_matrix(bie_ctx ctx, bie_matrix M, const double* rhs, int nrhs, double* x,
+                            const bie_solve_opts* opts, bie_solve_report* report);
 bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const double* rhs, int nrhs,
                      double* x, const bie_solve_opts* opts, bie_solve_report* report);
 

@@ -44,7 +44,7 @@ class SolveOpts(ctypes.Structure):
 class SolveReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("fallback_used", ctypes.c_int)]
+                ("fallback_used", ctypes.c_int), ("matvecs", ctypes.c_int)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -179,6 +179,11 @@ _sig("bie_assemble", _i32, [_vp, _vp, _i32, _d, _d, _vp])
 _sig("bie_assemble_near", _i32, [_vp, _vp, _u, _d, _d, _d, _d, _d, _vp])
 _sig("bie_assemble_near_band", _i32, [_vp, _vp, _u, _d, _d, _d, _d, _d, _vp])
 _sig("bie_solve", _i32, [_vp, _i64, _vp, _vp, _i32, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)])
+_sig("bie_solve_matrix", _i32, [_vp, _vp, _vp, _i32, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)])
+_sig("bie_matrix_create", _i32, [_vp, _i64, _vp, _u, ctypes.POINTER(_vp)])
+_sig("bie_matrix_free", None, [_vp])
+_sig("bie_matrix_size", _i64, [_vp])
+_sig("bie_matrix_matvec", _i32, [_vp, _i32, _vp, _i32, _vp])
 _sig("bie_rhs", _i32, [_vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _d, _vp])
 _sig("bie_field_eval", _i32, [_vp, _vp, _i32, _d, _d, _vp, _vp, _i64, _i32, _vp])
 
@@ -218,13 +223,12 @@ def assemble_near_band(surface, kernels, k, out=None, ws=1.0, wk=0.0, host=False
     return out
 
 
-def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,
-          surface=None, k=0.0, raise_on_noconv=True):
-    """FGMRES solve of A x = b (b: [N] or [nrhs, N]); returns (x, report dict).
+STORE_FP32, STORE_BF16X2 = 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16X2, PREC_DW = 0, 1, 2, 3
 
-    precond: 0 none, 1 block-diagonal (block), 2 learned (net on the grid of surface, wavenumber k,
-    on top of block if given; falls back to block when it does not converge)."""
-    n = A.shape[0]
+
+def _solve_call(fn, ctx, target, n, b, x, tol, restart, maxit, prec, precond, block, net, surface, k,
+                raise_on_noconv):
     bb = b.reshape(-1, n).contiguous()
     nrhs = bb.shape[0]
     if x is None:
@@ -232,12 +236,50 @@ def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=
     o = SolveOpts(tol, restart, maxit, prec, precond, block.h if block is not None else None,
                   net.h if net is not None else None, surface.h if surface is not None else None, float(k))
     r = SolveReport()
-    st = lib.bie_solve(ctx.h, n, _ptr(A), _ptr(bb), nrhs, _ptr(x), ctypes.byref(o), ctypes.byref(r))
+    st = fn(ctx.h, *target, _ptr(bb), nrhs, _ptr(x), ctypes.byref(o), ctypes.byref(r))
     rep = {"iterations": r.iterations, "refinements": r.refinements, "rel_residual": r.rel_residual,
-           "seconds": r.seconds, "fallback_used": r.fallback_used, "status": st}
+           "seconds": r.seconds, "fallback_used": r.fallback_used, "matvecs": r.matvecs, "status": st}
     if st != 4 or raise_on_noconv:   # 4 = BIE_ENOCONV: the report still holds the iterations and residual
         check(st, "bie_solve")
     return x.reshape(b.shape), rep
+
+
+def solve(ctx, A, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,
+          surface=None, k=0.0, raise_on_noconv=True):
+    """FGMRES solve of A x = b (b: [N] or [nrhs, N], right-hand sides in lockstep); returns (x, report).
+
+    prec: 0 FP64, 1 FP32 storage + FP64-accurate refinement, 2 split-BF16 tensor-core products +
+    refinement.  precond: 0 none, 1 block-diagonal (block), 2 learned (net on the grid of surface,
+    wavenumber k, on top of block if given; falls back to block when it does not converge)."""
+    n = A.shape[0]
+    return _solve_call(lib.bie_solve, ctx, (n, _ptr(A)), n, b, x, tol, restart, maxit, prec, precond, block, net,
+                       surface, k, raise_on_noconv)
+
+
+class Matrix:
+    """An FP64 system matrix (kept by the caller) with the low-precision copies the mixed solves read."""
+
+    def __init__(self, ctx, A, store=0):
+        self.ctx, self.A, self.n = ctx, A, A.shape[0]
+        self.h = _vp()
+        check(lib.bie_matrix_create(ctx.h, self.n, _ptr(A), int(store), ctypes.byref(self.h)), "bie_matrix_create")
+
+    def matvec(self, x, prec=PREC_FP64, out=None):
+        """y = A x for x [n] or [nr, n] (nr <= 16)."""
+        xx = x.reshape(-1, self.n).contiguous()
+        y = torch.empty_like(xx) if out is None else out
+        check(lib.bie_matrix_matvec(self.h, int(prec), _ptr(xx), xx.shape[0], _ptr(y)), "bie_matrix_matvec")
+        return y.reshape(x.shape)
+
+    def solve(self, b, x=None, tol=1e-8, restart=100, maxit=2000, prec=0, precond=0, block=None, net=None,
+              surface=None, k=0.0, raise_on_noconv=True):
+        return _solve_call(lib.bie_solve_matrix, self.ctx, (self.h,), self.n, b, x, tol, restart, maxit, prec,
+                           precond, block, net, surface, k, raise_on_noconv)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bie_matrix_free(self.h)
+            self.h = None
 
 
 _sig("bie_blockdiag_create", _i32, [_vp, _i64, _vp, _i32, ctypes.POINTER(_vp)])

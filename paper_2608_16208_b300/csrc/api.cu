@@ -78,6 +78,11 @@ bie_status bie_ctx_sync(bie_ctx ctx) {
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
     return BIE_EINVAL;
   }
+  if (st[1]) {
+    bie::set_error("a bounded device wait expired (tensor-core product)");
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
+    return BIE_ETIMEOUT;
+  }
   return BIE_OK;
 }
 

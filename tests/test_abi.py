@@ -57,6 +57,9 @@ def test_invalid_arguments_are_refused_before_any_device_call():
         "bie_field_eval": (null, null, i32(0), d(1.0), d(1.0), null, null, i64(1), i32(0), null),
         "bie_blockdiag_create": (null, i64(64), null, i32(32), null),
         "bie_batch_create": (null, i32(1), null, null, u(1), null, i64(1), null),
+        "bie_matrix_create": (null, i64(4), null, u(0), null),
+        "bie_matrix_matvec": (null, i32(0), null, i32(1), null),
+        "bie_solve_matrix": (null, null, null, i32(1), null, null, null),
     }
     for name, args in calls.items():
         fn = getattr(lib, name)
