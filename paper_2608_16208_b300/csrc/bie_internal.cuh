@@ -17,6 +17,10 @@ namespace bie {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kTwoPi = 6.283185307179586476925286766559005768;
 constexpr double kStableDelta = 0.06;  // |t - t_s| + |th - th_s| below which differences use the line integral
+// ... or |r_s - r| below which they do: next to a pole (J ~ sin t -> 0) a whole ring of source
+// angles is physically close to the target, and plain subtraction would cost tau_0 ~ kappa rho^2/2
+// a relative error ~2 eps |r| / (kappa rho^2)
+constexpr double kStableDist = 0.06;
 constexpr double kRootTol = 1e-14;     // Newton stops when |dz| <= tol*b + 4e-16|z| (then one more step)
 constexpr double kSeriesX = 0.5;       // alpha, beta by Taylor series when k rho < this
 constexpr double kSmallB = 0.1;        // translated swapping for tau_3 when b < this

@@ -172,10 +172,10 @@ __device__ __forceinline__ PairInfo bcast(const PairInfo& p, int src) {
 __device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, cplx z, cplx* f, cplx* df) {
   C3 r, rt, rth;
   surf_eval_c(S, P.ts, z, &r, &rt, &rth);
-  C3 Y;
-  const bool near = fabs(P.ts - P.t) + fabs(wrap_pi(z.re - P.th)) <= kStableDelta;
+  C3 Y = {r.x - C(P.x), r.y - C(P.y), r.z - C(P.z)};
+  const bool near = fabs(P.ts - P.t) + fabs(wrap_pi(z.re - P.th)) <= kStableDelta ||
+                    abs2(Y.x) + abs2(Y.y) + abs2(Y.z) <= kStableDist * kStableDist;
   if (near) Y = diff_ana<cplx>(S, P.ts, z, P.t, P.th);
-  else Y = {r.x - C(P.x), r.y - C(P.y), r.z - C(P.z)};
   *f = Y.x * Y.x + Y.y * Y.y + Y.z * Y.z;
   *df = 2.0 * (Y.x * rth.x + Y.y * rth.y + Y.z * rth.z);
 }
@@ -201,7 +201,8 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
     if (fabs(step) <= 1e-15 * (1 + fabs(a0))) break;
   }
   eval_r(a0);
-  if (fabs(P.ts - P.t) + fabs(wrap_pi(a0 - P.th)) <= kStableDelta) {   // rho^2(a0) without cancellation
+  if (fabs(P.ts - P.t) + fabs(wrap_pi(a0 - P.th)) <= kStableDelta || g0 <= kStableDist * kStableDist) {
+    // rho^2(a0) without cancellation
     const R3 Y = diff_ana<double>(S, P.ts, a0, P.t, P.th);
     g0 = dot(Y, Y);
   }
@@ -322,6 +323,7 @@ __device__ inline double sin_k_minus(int k, double x) {
 struct Smem {
   double *sn, *tau0, *bt0, *hr, *alph, *Acal, *Bcal;
   cplx *W0, *W1, *ph, *kc, *kk;
+  unsigned* nearbits;   // double layer: samples whose differences take the cancellation-free forms
 };
 
 // Per-warp shared memory of the pair pipeline, in doubles.  Single layer: sn, A~, the two
@@ -333,6 +335,7 @@ __host__ __device__ inline size_t smem_doubles(int Mt, int P, int L, bool withK)
   size_t d = 0;
   d += Mt;                                   // sn
   d += withK ? 4 * Mt : 0;                   // tau0, bt0, hr, alph
+  d += withK ? (Mt + 63) / 64 : 0;           // nearbits (one bit per sample)
   d += P;                                    // Acal
   d += withK ? P : 0;                        // Bcal
   d += d & 1;                                // W0, W1 start on 16 bytes: the transforms read float4
@@ -347,7 +350,10 @@ __device__ inline Smem carve(double* base, int Mt, int P, int L, bool withK) {
   Smem s = {};
   double* p = base;
   s.sn = p; p += Mt;
-  if (withK) { s.tau0 = p; p += Mt; s.bt0 = p; p += Mt; s.hr = p; p += Mt; s.alph = p; p += Mt; }
+  if (withK) {
+    s.tau0 = p; p += Mt; s.bt0 = p; p += Mt; s.hr = p; p += Mt; s.alph = p; p += Mt;
+    s.nearbits = reinterpret_cast<unsigned*>(p); p += (Mt + 63) / 64;
+  }
   s.Acal = p; p += P;
   if (withK) { s.Bcal = p; p += P; }
   p += (p - base) & 1;   // 16-byte start for the double-word transforms
@@ -653,13 +659,11 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
       for (int q = lane; q < Mt; q += 32) {
         const double thq = a.thg[3 * q];
         const int dq = q > i ? q - i : i - q;
-        double r2;
-        if (min(dq, Mt - dq) <= kn) {
+        const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
+        double r2 = yx * yx + yy * yy + yz * yz;
+        if (min(dq, Mt - dq) <= kn || r2 <= kStableDist * kStableDist) {
           const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
           r2 = dot(Y, Y);
-        } else {
-          const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
-          r2 = yx * yx + yy * yy + yz * yz;
         }
         rho2[q] = r2;
         bv = fmin(bv, r2);
@@ -806,17 +810,19 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       // ---- D3. samples
       double sha, cha;   // sin(a/2), cos(a/2)
       sincos(0.5 * ra, &sha, &cha);
+      for (int w = lane; w < (Mt + 31) / 32; w += 32) sm.nearbits[w] = 0u;
+      __syncwarp();
       for (int q = lane; q < Mt; q += 32) {
         const double thq = a.thg[3 * q];
-        const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta;
-        double yx, yy, yz;
+        double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
+        double r2 = yx * yx + yy * yy + yz * yz;
+        const bool near = dts + fabs(wrap_pi(pr.th - thq)) <= kStableDelta || r2 <= kStableDist * kStableDist;
         if (near) {
           const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
           yx = Y.x; yy = Y.y; yz = Y.z;
-        } else {
-          yx = rr[3 * q] - pr.x; yy = rr[3 * q + 1] - pr.y; yz = rr[3 * q + 2] - pr.z;
+          r2 = yx * yx + yy * yy + yz * yz;
+          atomicOr(&sm.nearbits[q >> 5], 1u << (q & 31));
         }
-        const double r2 = yx * yx + yy * yy + yz * yz;
         const double rinv = rsqrt(r2);
         const double rho = r2 * rinv;
         // sin((th_q - a)/2): direct where th_q - a is small (exact difference, relative accuracy),
@@ -855,16 +861,20 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       }
       __syncwarp();
       {
-        // tau_0 of near samples: second-derivative line integral (Section 4 Remark), 16 lanes per sample
-        const int i = (int)(pr.row % Mt);
-        const int Kw = (int)ceil(kStableDelta * Mt / kTwoPi) + 1;
-        for (int c0 = -Kw; c0 <= Kw; c0 += 2) {
-          const int c = c0 + (lane >> 4);
-          const int q = wrapi(i + c, Mt);
+        // tau_0 of near samples: second-derivative line integral (Section 4 Remark), 16 lanes per
+        // sample, two samples at a time, taken from the near bits of D3
+        for (int wd = 0; wd < (Mt + 31) / 32; ++wd) {
+          unsigned bits = sm.nearbits[wd];
+          while (bits) {
+            const int qa = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int qb = bits ? __ffs(bits) - 1 : -1;
+            if (bits) bits &= bits - 1;
+          const int qsel = (lane >> 4) ? qb : qa;
+          const bool nearq = qsel >= 0;
+          const int q = 32 * wd + (nearq ? qsel : 0);
           const double thq = a.thg[3 * q];
           const double dth = wrap_pi(pr.th - thq);
-          const bool nearq = (c <= Kw) && (dts + fabs(dth) <= kStableDelta);
-          if (!__ballot_sync(0xffffffffu, nearq)) continue;
           double acc = 0.0;
           if (nearq) {
             const int jn = lane & 15;
@@ -879,6 +889,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
           if (nearq && (lane & 15) == 0) sm.tau0[q] = acc;
           __syncwarp();
+          }
         }
         __syncwarp();
         for (int q = lane; q < Mt; q += 32) {
@@ -941,12 +952,11 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       double H3a = 0.0, H3pa = 0.0;
       if (translated) {
         // ---- D7. H3(a), H3'(a) directly from the geometry at th_s = a
-        const bool neara = dts + fabs(wrap_pi(ra - pr.th)) <= kStableDelta;
-        R3 Y;
         Geo G;
         surf_eval(a.S, pr.ts, ra, 2, &G);
+        R3 Y = {G.r.x - pr.x, G.r.y - pr.y, G.r.z - pr.z};
+        const bool neara = dts + fabs(wrap_pi(ra - pr.th)) <= kStableDelta || dot(Y, Y) <= kStableDist * kStableDist;
         if (neara) Y = diff_ana<double>(a.S, pr.ts, ra, pr.t, pr.th);
-        else Y = {G.r.x - pr.x, G.r.y - pr.y, G.r.z - pr.z};
         const R3 n = cross(G.rt, G.rth);
         const double J = sqrt(dot(n, n));
         const R3 nu = {n.x / J, n.y / J, n.z / J};

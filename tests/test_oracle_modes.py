@@ -48,6 +48,23 @@ def test_method_matches_definition(surface, Mt, k, dt):
         assert _rel(out[kd][0], d) <= 1e-12, kd
 
 
+@pytest.mark.parametrize("Mt", [64, 192])
+def test_method_matches_definition_next_to_a_pole(Mt):
+    """Targets and source rings within 0.003 of the pole t = 0 (J ~ sin t): the whole ring is physically
+    close, so its differences and tau_0 must take the cancellation-free forms (Section 4 Remark) beyond
+    the parameter window.  With plain subtraction there, tau_0 ~ kappa rho^2 / 2 carries relative errors
+    ~1e-10 and the brute-force definition itself does not converge (method vs definition 2.8e-9 for K)."""
+    surface, k = wl.harmonic_star(0, 300, 0.12), 12.0
+    t = np.array([0.0020811215478220846, 0.0020811215478220846, 0.0011])
+    ts = np.array([0.0022492321685155803, 0.0005, 0.0029])
+    th = 2 * np.pi * np.array([0, 3, 11]) / Mt
+    out = km.method_modes(surface, t, th, ts, Mt, k, ("S", "K", "Kp"))
+    for i in range(len(t)):
+        for kd in ("S", "K", "Kp"):
+            d, _ = km.definition_modes(surface, t[i], th[i], ts[i], Mt // 2, k, kd)
+            assert _rel(out[kd][i], d) <= 1e-12, (i, kd, _rel(out[kd][i], d))
+
+
 def test_recurrence_identity_and_conjugate_symmetry():
     # Eq. (iter:formula): sum_n (2m+n) <rho^2>_n <rho^{-1}>_{-(m+n)} = 0 ; <rho^{-1}>_{-l} = conj <rho^{-1}>_l
     Mt, M = 64, 32
