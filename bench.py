@@ -37,7 +37,12 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 WORKLOAD = "ellipsoid_np16_m128_k10"
-METRIC = "kernel-mode pairs/s (correction stage, S kernel, FP64)"
+METRIC = "kernel-mode pairs/s (correction stage, S kernel)"
+# what the headline's arithmetic is: the per-pair root, recurrences and samples in FP64; the
+# transforms, products and unpacking in double-word FP32 pairs (about 48 significant bits)
+PRECISION = {"root_newton": "f64", "a_m_recurrences": "f64", "samples_rho2_F_phases": "f64",
+             "transforms_products_unpacking": "double-word f32x2 (about 2^-48 per operation)",
+             "outputs": "f64", "parity_bound_per_pair": 1e-12}
 UNIT = "pairs/s"
 def _hbm_peak():
     """Measured copy bandwidth of the B300s (GB/s) and its source."""
@@ -120,32 +125,62 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def oracle_pairs_per_second(c, seconds=15.0, max_pairs=20000):
-    """Oracle (method mode) on a bounded sample of the workload's near pairs."""
+def host_cores():
+    """Host CPU threads this process may run on, and the CPU model (read at run time)."""
     try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:          # the oracle's numpy calls here are single-threaded anyway
-        import contextlib
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return n, model
 
-        def threadpool_limits(limits=None):
-            return contextlib.nullcontext()
+
+def _oracle_worker(job):
+    """One host process: the oracle's method mode on its own slice of pairs for a bounded time."""
+    surface, Mt, k, t, th, ts, seconds = job
     from oracle import kernel_modes as km
+    done = 0
+    t0 = time.perf_counter()
+    while done < len(t) and time.perf_counter() - t0 < seconds:
+        sl = slice(done, done + 64)
+        km.method_modes(surface, t[sl], th[sl], ts[sl], Mt, k, ("S",))
+        done += len(t[sl])
+    return done, time.perf_counter() - t0
+
+
+def oracle_pairs_per_second(c, seconds=15.0, max_pairs=None, cores=None):
+    """Oracle (method mode, S) on a bounded sample of the workload's near pairs, one single-threaded
+    process per host core (spawned), each on its own slice of pairs; rate = all pairs / the longest
+    process's time.  Returns (pairs/s, pairs, seconds, cores)."""
+    import multiprocessing as mp
     from oracle import nystrom as ny
+    cores = cores or host_cores()[0]
     gx = wl.load_ggq()[0]
-    rows = wl.sample_rows(c["Np"], c["Mt"], 400, seed=1)
+    rows = wl.sample_rows(c["Np"], c["Mt"], max(400, 40 * cores), seed=1)
     pairs = ny.near_pairs(c["Np"], c["Mt"], rows, gx)
+    if max_pairs:
+        pairs = pairs[:max_pairs]
     t = np.array([p[3] for p in pairs])
     th = np.array([p[4] for p in pairs])
     ts = np.array([p[5] for p in pairs])
-    done = 0
-    t0 = time.perf_counter()
-    with threadpool_limits(limits=1):
-        while done < min(len(t), max_pairs) and time.perf_counter() - t0 < seconds:
-            sl = slice(done, done + 128)
-            km.method_modes(c["surface"], t[sl], th[sl], ts[sl], c["Mt"], c["k"], ("S",))
-            done += len(t[sl])
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    per = -(-len(t) // cores)
+    jobs = [(c["surface"], c["Mt"], c["k"], t[i * per:(i + 1) * per], th[i * per:(i + 1) * per],
+             ts[i * per:(i + 1) * per], seconds) for i in range(cores) if i * per < len(t)]
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"      # inherited by the spawned processes: one thread each
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    done = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return done / dt, done, dt, len(jobs)
 
 
 def run_reference(args):
@@ -153,19 +188,21 @@ def run_reference(args):
     if rank != 0:
         return
     c = wl.config(WORKLOAD)
+    cores, model = host_cores()
     vals = []
     for _ in range(args.warmup):
-        oracle_pairs_per_second(c, seconds=5.0, max_pairs=512)
+        oracle_pairs_per_second(c, seconds=2.0, cores=cores)
     for _ in range(args.steps):
-        v, n, dt = oracle_pairs_per_second(c, seconds=10.0, max_pairs=2048)
+        v, n, dt, used = oracle_pairs_per_second(c, seconds=6.0, cores=cores)
         vals.append((v, n, dt))
     value = float(np.mean([v for v, _, _ in vals]))
-    sample = "%d steps of up to 2048 near pairs (10 s cap each) from 400 seeded target rows" % args.steps
+    sample = ("%d steps, each up to 6 s of near pairs of seeded target rows on %d single-threaded processes "
+              "(%s)" % (args.steps, used, model))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean([d for _, _, d in vals])),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_json(c),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -272,6 +309,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     pk_ms = float(np.mean([a.elapsed_time(b) for a, b in pk_events]))
     pk_pairs = rows_all.numel()
+    # accuracy of the timed launch: 256 seeded pairs of its output against the oracle, one by one
+    pick = np.unique(wl.Stream(11, 4).integers(0, pk_pairs - 1, 256))
+    pick_d = torch.from_numpy(pick).to(dev)
+    acc_rows, acc_srcs = rows_all[pick_d].cpu().numpy(), srcs_all[pick_d].cpu().numpy()
+    acc_got = modes[pick_d, 0].cpu().numpy()
     del modes
     # the single and double layer together over the same pairs (fused FP64 kernel), reported apart
     modes_sk = torch.empty((rows_all.numel(), 2, Mt + 1), dtype=torch.complex128, device=dev)
@@ -307,33 +349,31 @@ def run_gpu(args):
     del host_band
     h2d = 8 * (3 * 16 * 16 * 2 + 32) + 5 * 8 * len(c["surface"].get("terms", []))
 
-    # time to a 1e-8 residual: FP64 vs FP32 storage with FP64 refinement (plane wave along +z)
+    acc = accuracy_vs_oracle(c, acc_rows, acc_srcs, acc_got)
+
+    # time to a 1e-8 residual: FP64 vs the mixed solves, on this workload (4 plane waves + a point
+    # source) and on the bumpy surface at k = 20 (N = 49,152; plane wave + point source)
     solve = None
     if not args.skip_solve:
-        torch.cuda.synchronize()
-        # exterior sound-soft problem, combined-field operator on the unweighted density (second kind)
-        Afull = bie.assemble(surf, bie.OP_CFIE | bie.UNWEIGHTED, k, out=A)
-        g = bie.rhs(surf, 0, c["dirs"][0], k)
-        res = {}
-        for name, prec in (("fp64", 0), ("mixed_fp32_refined", 1)):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            try:
-                x, rep = bie.solve(ctx, Afull, g, tol=1e-8, restart=200, maxit=3000, prec=prec)
-                rep["wall_s"] = time.perf_counter() - t0
-            except bie.BieError as exc:
-                rep = {"error": str(exc)}
-            res[name] = rep
-        res["operator"] = "I + K - i k S (combined field, unweighted density), plane wave"
-        res["learned"] = run_learned(bie) if args.learned else None
-        solve = res
-
-    rows = run_rows(bie, surf, k, A, flush, stream, step_ms, solve)
+        solve = {"ellipsoid_np16_m128_k10": run_solves(bie, ctx, surf, c, A)}
+        mv_rows = solve["ellipsoid_np16_m128_k10"]
+        rows = run_rows(bie, surf, k, A, flush, stream, step_ms, mv_rows)
+        del A
+        torch.cuda.empty_cache()
+        c4 = wl.config("bumpy_np24_m128_k20")
+        s4 = bie.Surface(ctx, c4["surface"], c4["Np"], c4["Mt"], ggq)
+        solve["bumpy_np24_m128_k20"] = run_solves(bie, ctx, s4, c4, None)
+        del s4
+        torch.cuda.empty_cache()
+        solve["learned"] = run_learned(bie) if args.learned else None
+    else:
+        rows = run_rows(bie, surf, k, A, flush, stream, step_ms, None)
 
     batch = None if args.batch_surfaces <= 0 else run_batch(bie, ctx, args.batch_surfaces, stream)
 
     if rank == 0:
-        cpu_v, cpu_n, cpu_dt = oracle_pairs_per_second(c, seconds=15.0)
+        cpu_v, cpu_n, cpu_dt, cpu_cores = oracle_pairs_per_second(c, seconds=12.0)
+        cpu_model = host_cores()[1]
         cs = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -350,8 +390,11 @@ def run_gpu(args):
                          "flops_per_pair": fl, "step_gflops": step_gflops},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": float(np.median(e2e_ms))},
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d near pairs of 400 seeded target rows, method mode, %.1f s" % (cpu_n, cpu_dt)},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
+                             "sample": "%d near pairs of seeded target rows, method mode, %.1f s on %d "
+                                       "single-threaded processes (%s)" % (cpu_n, cpu_dt, cpu_cores, cpu_model)},
+            "precision": PRECISION,
+            "accuracy_vs_oracle": acc,
             "solve": solve,
             "batch": batch,
             "rows": rows,
@@ -361,6 +404,76 @@ def run_gpu(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def accuracy_vs_oracle(c, rows, srcs, got):
+    """Normwise error, per pair, of sampled outputs of the timed launch against the oracle's method
+    mode (max_m |gpu - oracle| / max_m |oracle|)."""
+    from oracle import kernel_modes as km
+    from oracle import nystrom as ny
+    gx = wl.load_ggq()[0]
+    Np, Mt = c["Np"], c["Mt"]
+    t_nodes, h = ny.nodes(Np)
+    tn, i, d, g = rows // Mt, rows % Mt, srcs // 16, srcs % 16
+    ts = (tn // 16 + d - 1 + 0.5) * h + (h / 2) * gx[d, tn % 16, g]
+    ref = np.concatenate([km.method_modes(c["surface"], t_nodes[tn[q:q + 128]], 2 * np.pi * i[q:q + 128] / Mt,
+                                          ts[q:q + 128], Mt, c["k"], ("S",))["S"] for q in range(0, len(rows), 128)])
+    err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    return {"pairs": int(len(rows)), "max_normwise": float(err.max()), "median_normwise": float(np.median(err)),
+            "kernel": "S", "sample": "seeded pairs of the timed kernel-modes launch over every near pair"}
+
+
+def run_solves(bie, ctx, surf, c, A=None):
+    """Time to a 1e-8 relative residual for the exterior sound-soft problem through the combined-field
+    operator I + K - i k S (unweighted density), all right-hand sides in lockstep (plane waves along the
+    workload's directions and the interior point source): FP64 products throughout; FP32 storage inside
+    FGMRES; split-BF16 storage on the tensor cores inside FGMRES (both with FP64-accurate refinement).
+    The matrix is assembled once; its FP32 and split-BF16 copies are made once (timed apart)."""
+    import torch
+    k = c["k"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A = bie.assemble(surf, bie.OP_CFIE | bie.UNWEIGHTED, k, out=A)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    B = torch.stack([bie.rhs(surf, 0, d, k) for d in c["dirs"]] + [bie.rhs(surf, 1, c["src"], k)])
+    t0 = time.perf_counter()
+    M = bie.Matrix(ctx, A, bie.STORE_FP32 | bie.STORE_BF16X2)
+    torch.cuda.synchronize()
+    t_copy = time.perf_counter() - t0
+    dirs = wl.Stream(0, 21).directions(32)
+    out = {"unknowns": surf.N, "rhs": int(B.shape[0]), "k": k, "tol": 1e-8,
+           "operator": "I + K - i k S (combined field, unweighted density)",
+           "assemble_s": t_asm, "low_precision_copies_s": t_copy, "far_field_directions": 32}
+    ff = {}
+    for name, prec in (("fp64", 0), ("mixed_fp32", 1), ("mixed_bf16x2_tensor_cores", 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            X, rep = M.solve(B, tol=1e-8, restart=200, maxit=3000, prec=prec)
+            rep["wall_s"] = time.perf_counter() - t0
+            rep["ms_per_iteration"] = 1000.0 * rep["seconds"] / max(1, rep["iterations"])
+            ff[name] = np.stack([bie.field_eval(surf, bie.OP_CFIE | bie.UNWEIGHTED, k, X[j].contiguous(), dirs,
+                                                far_field=True).cpu().numpy() for j in range(B.shape[0])])
+        except bie.BieError as exc:
+            rep = {"error": str(exc)}
+        out[name] = rep
+    # far-field errors: against the FP64 solve (every right-hand side) and, for the point source, against
+    # its exact far field e^{-ik d.x_src} / (4 pi) (the manufactured solution)
+    exact = np.exp(-1j * k * (dirs @ np.asarray(c["src"], float))) / (4 * np.pi)
+    for name, u in ff.items():
+        e = {"point_source_vs_exact": float(np.linalg.norm(u[-1] - exact) / np.linalg.norm(exact))}
+        if name != "fp64" and "fp64" in ff:
+            ref = ff["fp64"]
+            e["vs_fp64_max_over_rhs"] = float(max(np.linalg.norm(u[j] - ref[j]) / np.linalg.norm(ref[j])
+                                                  for j in range(len(u))))
+        out[name]["far_field_error"] = e
+    if "seconds" in out.get("fp64", {}):
+        for name in ("mixed_fp32", "mixed_bf16x2_tensor_cores"):
+            if "seconds" in out.get(name, {}):
+                out[name]["speedup_vs_fp64"] = out["fp64"]["seconds"] / out[name]["seconds"]
+    del M
+    return out
 
 
 def run_batch(bie, ctx, count, stream):
@@ -512,17 +625,28 @@ def run_rows(bie, surf, k, A, flush, stream, near_ms, solve):
         "write_GBps": 16.0 * N * N / (far_ms / 1000.0) / 1e9, "hbm_peak_GBps": hbm, "hbm_peak_source": hbm_src,
         "frac_of_hbm": 16.0 * N * N / (far_ms / 1000.0) / 1e9 / hbm,
         "bound": "FP64: one rsqrt and one sincos per entry (writes 16 B per entry)"}
+    # block products alone (5 right-hand sides, one pass over the matrix each), timed with events
+    M = bie.Matrix(surf.ctx, A, bie.STORE_FP32 | bie.STORE_BF16X2)
+    X = torch.as_tensor(wl.random_complex((5, N), 3, 7), dtype=torch.complex128).cuda()
+    mv = {}
+    for name, prec, bytes_per in (("fp64", 0, 16), ("fp32", 1, 8), ("bf16x2_tensor_cores", 2, 8),
+                                  ("fp64_storage_double_word", 3, 16)):
+        ms_ = timed(lambda: M.matvec(X, prec))
+        mv[name] = {"ms": ms_, "matrix_bytes": bytes_per * N * N, "rhs": 5,
+                    "read_GBps": bytes_per * N * N / (ms_ / 1000.0) / 1e9,
+                    "frac_of_hbm": bytes_per * N * N / (ms_ / 1000.0) / 1e9 / hbm}
+    mv["hbm_peak_GBps"] = hbm
+    rows["block_product"] = mv
+    del M, X
     if solve is not None:
-        mv = {}
-        for name, bytes_per in (("fp64", 16), ("mixed_fp32_refined", 8)):
+        it = {}
+        for name in ("fp64", "mixed_fp32", "mixed_bf16x2_tensor_cores"):
             rep = solve.get(name, {})
             if rep.get("iterations"):
-                per = 1000.0 * rep["seconds"] / rep["iterations"]
-                mv[name] = {"ms_per_iteration": per, "matrix_bytes": bytes_per * N * N,
-                            "implied_read_GBps": bytes_per * N * N / (per / 1000.0) / 1e9}
-        mv["note"] = ("iteration time covers the matvec, the Arnoldi step and, for the mixed solve, its "
-                      "share of the FP64 refinement residuals; the implied rate is a lower bound on the matvec's")
-        rows["matvec"] = mv
+                it[name] = {"ms_per_iteration": 1000.0 * rep["seconds"] / rep["iterations"], "rhs": solve["rhs"]}
+        it["note"] = ("iteration time covers the block product, the Arnoldi steps of every right-hand side and, for "
+                      "the mixed solves, their share of the FP64-accurate refinement residuals")
+        rows["fgmres_iteration"] = it
     pts = torch.as_tensor(wl.exterior_points(8192, 3.0), dtype=torch.float64).cuda()
     dens = torch.as_tensor(wl.random_complex((N,), 0, 13), dtype=torch.complex128).cuda()
     fe_ms = timed(lambda: bie.field_eval(surf, bie.OP_S, k, dens, pts))

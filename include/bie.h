@@ -58,13 +58,18 @@ typedef struct bie_batch_s* bie_batch;
 /* ---- kernels and operators ------------------------------------------------ */
 #define BIE_KERNEL_S 1u  /* e^{ik rho}/rho                      (Section 3, Eq. (Sphi:appr2)) */
 #define BIE_KERNEL_K 2u  /* alpha tau1 - tau3 - i beta tau0      (Section 4, Eq. (dis:K))      */
+#define BIE_KERNEL_KP 4u /* the same with tau0 = nu(x).(x - y), the target's normal
+                            (Section 4, the integrand of the adjoint double layer K')        */
 
 typedef enum {
   BIE_OP_S = 0,          /* S                      (Eq. (bie:S))                          */
   BIE_OP_K = 1,          /* K                                                             */
   BIE_OP_K_PLUS_I = 2,   /* K + I  exterior Dirichlet, double layer (Eq. (bie:Kie))        */
   BIE_OP_K_MINUS_I = 3,  /* K - I  interior Dirichlet, double layer (Eq. (bie:Kie))        */
-  BIE_OP_CFIE = 4        /* I + K - i eta S: exterior Dirichlet, combined field           */
+  BIE_OP_CFIE = 4,       /* I + K - i eta S: exterior Dirichlet, combined field           */
+  BIE_OP_KP = 5,         /* K' (adjoint double layer)                                     */
+  BIE_OP_KP_PLUS_I = 6,  /* K' + I  interior Neumann (Eq. (bie:Kpie))                      */
+  BIE_OP_KP_MINUS_I = 7  /* K' - I  exterior Neumann (Eq. (bie:Kpie))                      */
 } bie_operator;
 
 /* ---- context ----------------------------------------------------------------
@@ -81,10 +86,25 @@ bie_status bie_ctx_sync(bie_ctx ctx);
 
 /* ---- surfaces (Section 2, Eq. (para); Section 3.1) -------------------------
  * kind 0, ellipsoid:  r = (a sin t cos th, b sin t sin th, c cos t), t in [0, pi]
+ *                     (axes = a, b, c)
  * kind 1, star:       r = h(t,th) (sin t cos th, sin t sin th, cos t),
  *                     h = 1 + sum_i c_i sin^p_i t cos^q_i t T_i(m_i th),
  *                     T = cos (s_i = 0) or sin (s_i = 1); terms[5*i..5*i+4] =
- *                     (c, p, q, m, s) as doubles, n_terms <= BIE_MAX_TERMS.   */
+ *                     (c, p, q, m, s) as doubles, n_terms <= BIE_MAX_TERMS.
+ * kind 2, bean (Section 5, Example 2, given there implicitly; parameterised
+ *                     by z = cos t and the angle th around each horizontal
+ *                     ellipse): r = (sqrt(A) sin t cos th, -0.3 u + sqrt(B) sin t
+ *                     sin th, cos t), u = cos(pi cos t), A = 0.64 (1 - 0.1 u),
+ *                     B = 0.64 (1 - 0.4 u); no parameters.
+ * kind 3, torus (Section 5, Example 3): r = (a w cos t, b w sin t, c sin th),
+ *                     w = R + cos th + eps cos(m t), t in [0, 2 pi] periodic;
+ *                     axes = (a, b, c), one term (R, eps, m, -, -).
+ * kind 4, Fourier torus (Section 5, Example 4): r = (w cos t, w sin t, zeta),
+ *                     w = R + sum c_i cos(m_i th + n_i t), zeta = sum c_i
+ *                     sin(m_i th + n_i t), t periodic; axes[0] = R, terms
+ *                     (c, m, n, -, -).
+ * On the tori (kinds 3, 4) the first and last panels are neighbours (Section
+ * 3.1, Remark): every panel has two near neighbours, and n_panels >= 3.      */
 #define BIE_MAX_TERMS 96
 typedef struct {
   int kind;
@@ -112,13 +132,13 @@ typedef struct {
  * normals, Jacobians and the data the pair pipeline needs (Section 2 and the
  * Section 4 Remark on second derivatives).  Allocates device memory owned by
  * the returned handle.  Np in [2, 4096]; Mth even, in [8, 1024], of the form
- * 2^a 3^b.  Errors: BIE_EINVAL, BIE_ENAN (a NaN or Inf in the descriptor or
+ * 2^a 3^b 5^c.  Errors: BIE_EINVAL, BIE_ENAN (a NaN or Inf in the descriptor or
  * the tables), BIE_ENOMEM, BIE_ECUDA.                                       */
 bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int n_panels,
                               int m_theta, const bie_quad_tables* ggq, bie_surface* out);
 void bie_surface_free(bie_surface s);
-/* Number of unknowns N = 16*Np*Mth, and number of near pairs
- * 256*Mth*(3Np-2) (targets x GGQ source nodes on the self and adjacent panels). */
+/* Number of unknowns N = 16*Np*Mth, and number of near pairs 256*Mth*(3Np-2)
+ * (3Np on a torus): targets x GGQ source nodes on the self and adjacent panels. */
 int64_t bie_surface_unknowns(bie_surface s);
 int64_t bie_surface_near_pairs(bie_surface s);
 /* [dev] views owned by the surface: node positions [N][3], unit normals [N][3],
@@ -130,8 +150,9 @@ const double* bie_surface_jacobians(bie_surface s);
 /* ---- kernel modes (Sections 3.2-3.3, 4) -----------------------------------
  * For each pair p = (target row, source) with target row = flat node index
  * (t_j^l, theta_i) and source = d*16 + g (the GGQ node g of the near panel
- * j + d - 1), write the theta_s-Fourier modes K_m, m = -M..M (M = Mth/2), of
- * each requested kernel (bit mask of BIE_KERNEL_*), computed by singularity
+ * j + d - 1, cyclic on a torus), write the theta_s-Fourier modes K_m,
+ * m = -M..M (M = Mth/2), of each requested kernel (bit mask of
+ * BIE_KERNEL_S, _K, _KP; any non-empty subset), computed by singularity
  * swapping: complex root of rho^2 by Newton, smooth factor F = (s_{a,b}/rho^2)^{1/2}
  * (Lemma "singular1"), A_m(b) by the difference recurrence or Miller's
  * recurrence (Eqs. (Am), (diff-recurrence)), zero-padded FFT convolution
@@ -210,8 +231,9 @@ void bie_batch_free(bie_batch plan);
 /* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------
  * Fill the dense N x N matrix of operator op acting on the weighted density:
  * preparation stage (Gauss-Legendre x trapezoid for every block) and
- * correction stage (near blocks |i-j| <= 1 from the pair pipeline, Parseval
- * weights, GGQ weights and Lagrange interpolation to the 16 Legendre nodes).
+ * correction stage (near blocks |i-j| <= 1, cyclically on a torus, from the
+ * pair pipeline, Parseval weights, GGQ weights and Lagrange interpolation to
+ * the 16 Legendre nodes).  op: a bie_operator, optionally | BIE_UNWEIGHTED.
  *   A_out [dev] double2[N][N] row-major (row = target), overwritten.
  *   eta   coupling of BIE_OP_CFIE (ignored otherwise).
  * Errors: BIE_EINVAL, BIE_ECUDA.                                              */
@@ -219,7 +241,8 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op, double k, double eta
 
 /* Correction stage only (the paper's dominant cost, Section 3.4): add
  * (ws_re + i ws_im) times the near-block entries of S and (wk_re + i wk_im)
- * times those of K (kernels = bit mask of BIE_KERNEL_*) to A_out [dev]
+ * times those of the double layer, K or K' (kernels = BIE_KERNEL_S with at
+ * most one of BIE_KERNEL_K, BIE_KERNEL_KP) to A_out [dev]
  * double2[N][N] (row = target).  Entries outside the near blocks are not
  * touched.  Uses a device work buffer of 16*48*Mth*Mth double2 (freed on
  * return, stream-ordered).  Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA.       */
@@ -401,7 +424,8 @@ bie_status bie_solve(bie_ctx ctx, int64_t n, const double* A, const double* rhs,
 /* ---- boundary data and fields (Section 3.4, Section 5) ---------------------
  * bie_rhs: g on the collocation nodes.  kind 0: plane wave, sound-soft,
  * g = -e^{ik d.x} (param = d[3]); kind 1: point source g = G(x; x_src)
- * (param = x_src[3]).  g [dev] double2[N].                                    */
+ * (param = x_src[3]), G = e^{ik|x-y|}/(4 pi |x-y|); kind 2: its normal
+ * derivative dG/dnu(x) (Neumann data, param = x_src[3]).  g [dev] double2[N]. */
 bie_status bie_rhs(bie_ctx ctx, bie_surface s, int kind, const double* param, double k, double* g);
 
 /* bie_field_eval: u(x_p) (far_field = 0) or the far-field pattern u_inf(d_p)

@@ -38,7 +38,7 @@ from . import geometry as geo
 from . import special as sp
 
 STABLE_DELTA = 0.06     # |t - t_s| + |th - th_s| below which differences use the line integral
-STABLE_DIST = 0.06      # ... or |r_s - r| below which they do (next to a pole, see _near_mask)
+STABLE_DIST = 0.06      # ... or |r_s - r| below which they do (next to a pole, see _near_difference)
 ROOT_TOL = 1e-14        # Newton stops when |dzeta| <= ROOT_TOL*b + 4e-16|zeta| (then one more step)
 SERIES_X = 0.5          # alpha(rho), beta(rho) use their Taylor series when k rho < SERIES_X
 SMALL_B = 0.1           # translated swapping for tau_3 when b < SMALL_B (the paper uses 0.01)
@@ -105,17 +105,23 @@ def alpha_beta(rho, k):
     return alpha, beta
 
 
-def _near_mask(surface, t_s, th_s, t, th):
-    """Samples whose difference r_s - r and tau_0 take the cancellation-free forms of the Section 4
-    Remark: within STABLE_DELTA in the parameters, or within STABLE_DIST in space.  The second
-    test matters next to a pole, where J ~ sin t vanishes: there a whole ring of source angles lies
-    physically close to the target, and plain subtraction would give tau_0 ~ kappa rho^2 / 2 an
-    absolute error ~eps |r|, i.e. a relative error ~2 eps |r| / (kappa rho^2) (1e-10 at rho = 1e-3).
-    For complex th_s the distance is the norm of the complex difference vector."""
-    par = np.abs(t_s - t) + np.abs(np.real(geo.wrap_angle(th_s - th))) <= STABLE_DELTA
+def _near_difference(surface, t_s, th_s, t, th):
+    """r(t_s, th_s) - r(t, th) and the mask of samples that take the cancellation-free forms of the
+    Section 4 Remark (line integrals for the difference and for tau_0): those within STABLE_DELTA in
+    the parameters, or within STABLE_DIST in space.  The second test matters next to a pole, where J ~
+    sin t vanishes: there a whole ring of source angles lies physically close to the target, and plain
+    subtraction would give tau_0 ~ kappa rho^2 / 2 an absolute error ~eps |r|, i.e. a relative error
+    ~2 eps |r| / (kappa rho^2) (1e-10 at rho = 1e-3).  For complex th_s the distance is the norm of the
+    complex difference vector."""
+    t_s, th_s, t, th = np.broadcast_arrays(np.asarray(t_s, float), np.asarray(th_s), np.asarray(t, float),
+                                           np.asarray(th))
     Y = geo.evaluate(surface, t_s, th_s)[0] - geo.evaluate(surface, t, th)[0]
-    phys = np.sum(np.abs(Y) ** 2, -1) <= STABLE_DIST ** 2
-    return par | phys
+    par = np.abs(t_s - t) + np.abs(np.real(geo.wrap_angle(th_s - th))) <= STABLE_DELTA
+    near = par | (np.sum(np.abs(Y) ** 2, -1) <= STABLE_DIST ** 2)
+    if np.any(near):
+        Y = Y.astype(np.result_type(Y, complex) if np.iscomplexobj(th_s) else Y.dtype)
+        Y[near] = geo.difference(surface, t_s[near], th_s[near], t[near], th[near], True)
+    return Y, near
 
 
 # ----------------------------------------------------------------------------
@@ -136,8 +142,7 @@ def locate_root(surface, t, th, t_s, thq, rho2):
     start = a0.copy()
 
     def deriv(z):
-        near = _near_mask(surface, t_s, z, t, th)
-        Y = geo.difference(surface, t_s, z, t, th, near)
+        Y, _ = _near_difference(surface, t_s, z, t, th)
         _, _, rth, _, _, rthth = geo.evaluate(surface, t_s, z)
         g0 = np.sum(Y * Y, -1)
         g1 = 2 * np.sum(Y * rth, -1)
@@ -184,8 +189,7 @@ def _pair_samples(surface, t, th, t_s, Mt):
     TH_s = np.broadcast_to(thq[None, :], (len(t), Mt))
     T = np.broadcast_to(t[:, None], (len(t), Mt))
     TH = np.broadcast_to(th[:, None], (len(t), Mt))
-    near = _near_mask(surface, T_s, TH_s, T, TH)
-    Y = geo.difference(surface, T_s, TH_s, T, TH, near)
+    Y, near = _near_difference(surface, T_s, TH_s, T, TH)
     return thq, T_s, TH_s, T, TH, near, Y
 
 
@@ -229,7 +233,7 @@ def method_modes(surface, t, th, t_s, Mt, k, kernels=("S",), return_details=Fals
             thf = 2 * np.pi * np.arange(n) / n
             Tsf, THsf = np.broadcast_to(t_s[:, None], (len(t), n)), np.broadcast_to(thf[None, :], (len(t), n))
             Tf, THf = np.broadcast_to(t[:, None], (len(t), n)), np.broadcast_to(th[:, None], (len(t), n))
-            Yf = geo.difference(surface, Tsf, THsf, Tf, THf, _near_mask(surface, Tsf, THsf, Tf, THf))
+            Yf, _ = _near_difference(surface, Tsf, THsf, Tf, THf)
             sf = (-np.expm1(-b))[:, None] ** 2 + 4 * q[:, None] * np.sin((thf[None, :] - a[:, None]) / 2) ** 2
             p = qq * M
             f = sym_modes(np.sqrt(sf / np.sum(Yf * Yf, -1)), p)
@@ -298,8 +302,7 @@ def h3_at_root(surface, t, th, t_s, a, b, f=None, target_normal=False):
     F is smooth, while the direct form -F (rho^2)'(a) / (2 rho^2(a)) divides an
     O(b^2) dot product of O(b) vectors by rho^2 and loses digits like eps/b.
     """
-    near = _near_mask(surface, t_s, a, t, th)
-    Y = geo.difference(surface, t_s, a, t, th, near)
+    Y, near = _near_difference(surface, t_s, a, t, th)
     _, rt, rth, _, rtth, rthth = geo.evaluate(surface, t_s, a)
     if target_normal:
         nu_x, _ = geo.normal_and_jacobian(surface, t, th)
@@ -397,8 +400,7 @@ def rho_inv_modes_banded(surface, t, th, t_s, lmax, eps0=1e-14):
     prev = None
     while True:
         thq = 2 * np.pi * np.arange(n) / n
-        near = _near_mask(surface, t_s, thq, t, th)
-        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        Y, near = _near_difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th))
         c = np.fft.fft(np.sum(Y * Y, -1)) / n
         if prev is not None and np.max(np.abs(c[:32] - prev[:32])) <= 1e-16 * np.max(np.abs(c)):
             break
@@ -439,8 +441,7 @@ def definition_rho_inv(surface, t, th, t_s, M, tol=1e-15, n_max=2 ** 22):
     prev = None
     while True:
         thq = 2 * np.pi * np.arange(n) / n
-        near = _near_mask(surface, t_s, thq, t, th)
-        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        Y, near = _near_difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th))
         c = np.fft.fft(1.0 / np.sqrt(np.sum(Y * Y, -1))) / n
         m = np.arange(-M, M + 1)
         cur = c[m % n]
@@ -459,8 +460,7 @@ def definition_modes(surface, t, th, t_s, M, k, kernel="S", n_start=None, tol=1e
     prev = None
     while True:
         thq = 2 * np.pi * np.arange(n) / n
-        near = _near_mask(surface, t_s, thq, t, th)
-        Y = geo.difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th), near)
+        Y, near = _near_difference(surface, np.full(n, t_s), thq, np.full(n, t), np.full(n, th))
         rho = np.sqrt(np.sum(Y * Y, -1))
         if kernel == "S":
             f = np.exp(1j * k * rho) / rho

@@ -17,8 +17,10 @@ if not os.path.exists(_LIB_PATH):
                       "(there is no CPU fallback)")
 lib = ctypes.CDLL(_LIB_PATH)
 
-KERNEL_S, KERNEL_K = 1, 2
-OP_S, OP_K, OP_K_PLUS_I, OP_K_MINUS_I, OP_CFIE = 0, 1, 2, 3, 4
+KERNEL_S, KERNEL_K, KERNEL_KP = 1, 2, 4
+OP_S, OP_K, OP_K_PLUS_I, OP_K_MINUS_I, OP_CFIE, OP_KP, OP_KP_PLUS_I, OP_KP_MINUS_I = 0, 1, 2, 3, 4, 5, 6, 7
+RHS_PLANE_WAVE, RHS_POINT_SOURCE, RHS_POINT_SOURCE_NORMAL_DERIVATIVE = 0, 1, 2
+_KINDS = {"ellipsoid": 0, "star": 1, "bean": 2, "torus": 3, "fourier_torus": 4}
 UNWEIGHTED = 0x100
 MAX_TERMS = 96
 
@@ -117,16 +119,25 @@ class Surface:
     def __init__(self, ctx, desc, Np, Mt, ggq):
         self.ctx, self.Np, self.Mt = ctx, Np, Mt
         d = SurfaceDesc()
-        d.kind = 0 if desc["kind"] == "ellipsoid" else 1
+        d.kind = _KINDS[desc["kind"]]
+        terms = None
         if d.kind == 0:
             d.axes[:] = list(desc["axes"])
-            d.n_terms = 0
-            self._terms = None
-        else:
-            terms = np.ascontiguousarray(np.asarray(desc["terms"], dtype=np.float64).reshape(-1, 5))
+        elif d.kind == 1:
+            terms = np.asarray(desc["terms"], dtype=np.float64).reshape(-1, 5)
+        elif d.kind == 3:   # torus: axes (a, b, c), one term (R, eps, m)
+            d.axes[:] = [desc["a"], desc["b"], desc["c"]]
+            terms = np.array([[desc["R"], desc["eps"], desc["m"], 0.0, 0.0]])
+        elif d.kind == 4:   # Fourier torus: axes[0] = R, terms (c, m, n)
+            d.axes[:] = [desc["R"], 0.0, 0.0]
+            tt = np.asarray(desc["terms"], dtype=np.float64).reshape(-1, 3)
+            terms = np.concatenate([tt, np.zeros((len(tt), 2))], axis=1)
+        self._terms = None
+        d.n_terms = 0
+        if terms is not None:
+            self._terms = np.ascontiguousarray(terms)
             d.n_terms = len(terms)
-            self._terms = terms
-            d.terms = terms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            d.terms = self._terms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         q = QuadTables()
         gx, gw = ggq[0], ggq[1]
         q.x[:] = np.ascontiguousarray(gx, dtype=np.float64).ravel().tolist()
@@ -397,7 +408,8 @@ class TrainSet:
 
 
 def rhs(surface, kind, param, k, out=None):
-    """Boundary data: kind 0 plane wave -e^{ik d.x} (param = d), kind 1 point source (param = source)."""
+    """Boundary data: kind 0 plane wave -e^{ik d.x} (param = d), kind 1 point source G(x; src), kind 2 its
+    normal derivative dG/dnu(x) (param = source; the Neumann data)."""
     if out is None:
         out = torch.empty(surface.N, dtype=torch.complex128, device="cuda")
     p = (ctypes.c_double * 3)(*[float(v) for v in param])

@@ -21,7 +21,8 @@ namespace bie {
 
 struct FarArgs {
   SurfP S;
-  int Np, Mt;
+  int Np, Mt, periodic;
+  int kprime;           // the double-layer part is K' (tau_0 with the target's normal)
   int64_t N;
   double h, k, wid;
   int unweighted;
@@ -61,12 +62,16 @@ __global__ void far_fill_kernel(const FarArgs a) {
     for (int row = r0; row < rend; ++row) {
       const int jrow = row / per_panel;
       cplx v = C(0.0);
-      if (abs(jcol - jrow) >= 2) {
+      int dj = abs(jcol - jrow);
+      if (a.periodic && a.Np - dj < dj) dj = a.Np - dj;   // torus: the first and last panels are neighbours
+      if (dj >= 2) {
         const double yx = sx - a.pts[3 * row], yy = sy - a.pts[3 * row + 1], yz = sz - a.pts[3 * row + 2];
         const double r2 = yx * yx + yy * yy + yz * yz;
         const double rinv = rsqrt(r2);
         const double x = a.k * (r2 * rinv);
-        const double tau0 = wantK ? nx * yx + ny * yy + nz * yz : 0.0;
+        const double tau0 = !wantK ? 0.0
+                            : a.kprime ? -(a.nrm[3 * row] * yx + a.nrm[3 * row + 1] * yy + a.nrm[3 * row + 2] * yz)
+                                       : nx * yx + ny * yy + nz * yz;
         if (x < kFarDwMaxPhase) {
           float2 sn, cs;
           dw_sincos(x, &sn, &cs);
@@ -111,14 +116,15 @@ struct NearOut {
 // kDW: single layer alone with double-word weights (re.h, re.l, im.h, im.l); the GGQ fold, the
 // scaling and the Jacobian run in double words, and only the update of A in FP64.
 template <bool kDW>
-__global__ void near_fill_kernel(int Np, int Mt, int jpanel, cplx sS, cplx sK,
+__global__ void near_fill_kernel(int Np, int Mt, int periodic, int jpanel, cplx sS, cplx sK,
                                  const double* __restrict__ coef, const float2* __restrict__ coefw,
                                  const cplx* __restrict__ WS, const cplx* __restrict__ WK,
                                  const double* __restrict__ jcol, const NearOut out) {
   const int tl = blockIdx.x;            // l * Mt + i
   const int d = blockIdx.y;
   const int l = tl / Mt, i = tl % Mt;
-  const int ip = jpanel + d - 1;
+  int ip = jpanel + d - 1;
+  if (periodic) ip = (ip + Np) % Np;   // torus: cyclic neighbours
   const bool inside = ip >= 0 && ip < Np;
   if (!inside && !out.band) return;
   const int64_t tn = (int64_t)jpanel * 16 + l;
@@ -183,7 +189,8 @@ extern "C" {
 static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, double k, cplx ws, cplx wk,
                              const double* jac, NearOut dst, cplx* host_band) {
   const int Mt = s->Mt;
-  const int nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + ((kernels & BIE_KERNEL_K) ? 1 : 0);
+  const unsigned dl = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);   // the double layer (at most one kind)
+  const int nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + (dl ? 1 : 0);
   const int64_t panel_pairs = (int64_t)16 * 48 * Mt;
   const int64_t panel_rows = (int64_t)16 * Mt;
   // panels per launch: enough pairs for many waves, weight buffer at most ~4 GB
@@ -237,15 +244,15 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
     st = launch_pairs(s, a);
     if (st != BIE_OK) break;
     const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
-    const cplx* WK = (kernels & BIE_KERNEL_K) ? W + (nk - 1) * a.weights_stride : nullptr;
+    const cplx* WK = dl ? W + (nk - 1) * a.weights_stride : nullptr;
     for (int jj = 0; jj < nj; ++jj) {
       const int64_t off = (int64_t)jj * panel_pairs * Mt;
       dim3 grid(16 * Mt, 3);
       if (dw)
-        near_fill_kernel<true><<<grid, 256, 0, st0>>>(s->Np, Mt, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
+        near_fill_kernel<true><<<grid, 256, 0, st0>>>(s->Np, Mt, s->sp.periodic, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
                                                       WS + off, nullptr, jac, o);
       else
-        near_fill_kernel<false><<<grid, 256, 0, st0>>>(s->Np, Mt, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
+        near_fill_kernel<false><<<grid, 256, 0, st0>>>(s->Np, Mt, s->sp.periodic, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
                                                        WS ? WS + off : nullptr, WK ? WK + off : nullptr, jac, o);
     }
     e = cudaGetLastError();
@@ -284,8 +291,9 @@ static bie_status check_near_args(const char* who, bie_ctx ctx, bie_surface s, u
                                   const void* out) {
   if (!ctx || !s || !out) { set_error("%s: NULL argument", who); return BIE_EINVAL; }
   if (!(k > 0) || !(k < 1e6)) { set_error("%s: k must be in (0, 1e6)", who); return BIE_EINVAL; }
-  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
-    set_error("%s: bad kernel mask %u", who, kernels);
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K | BIE_KERNEL_KP)) ||
+      ((kernels & BIE_KERNEL_K) && (kernels & BIE_KERNEL_KP))) {
+    set_error("%s: bad kernel mask %u (S and at most one of K, KP)", who, kernels);
     return BIE_EINVAL;
   }
   return BIE_OK;
@@ -320,7 +328,7 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   const bool unweighted = op_flags & BIE_UNWEIGHTED;
   const int op = op_flags & ~BIE_UNWEIGHTED;
   if (!ctx || !s || !A_out) { set_error("bie_assemble: NULL argument"); return BIE_EINVAL; }
-  if (op < BIE_OP_S || op > BIE_OP_CFIE) { set_error("bie_assemble: unknown operator %d", op); return BIE_EINVAL; }
+  if (op < BIE_OP_S || op > BIE_OP_KP_MINUS_I) { set_error("bie_assemble: unknown operator %d", op); return BIE_EINVAL; }
   if (!(k > 0) || !(k < 1e6)) { set_error("bie_assemble: k must be in (0, 1e6)"); return BIE_EINVAL; }
   cplx ws = C(0.0), wk = C(0.0);
   double wid = 0.0;
@@ -330,11 +338,17 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
     case BIE_OP_K_PLUS_I: wk = C(1.0); wid = 1.0; break;
     case BIE_OP_K_MINUS_I: wk = C(1.0); wid = -1.0; break;
     case BIE_OP_CFIE: wk = C(1.0); wid = 1.0; ws = C(0.0, -eta); break;
+    case BIE_OP_KP: wk = C(1.0); break;
+    case BIE_OP_KP_PLUS_I: wk = C(1.0); wid = 1.0; break;
+    case BIE_OP_KP_MINUS_I: wk = C(1.0); wid = -1.0; break;
   }
+  const bool kp = op >= BIE_OP_KP;
   FarArgs fa;
   fa.S = s->sp;
   fa.Np = s->Np;
   fa.Mt = s->Mt;
+  fa.periodic = s->sp.periodic;
+  fa.kprime = kp ? 1 : 0;
   fa.N = s->N;
   fa.h = s->h;
   fa.k = k;
@@ -354,7 +368,7 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   if (e != cudaSuccess) return cuda_fail(e, "far_fill_kernel");
   unsigned kernels = 0;
   if (ws.re != 0.0 || ws.im != 0.0) kernels |= BIE_KERNEL_S;
-  if (wk.re != 0.0 || wk.im != 0.0) kernels |= BIE_KERNEL_K;
+  if (wk.re != 0.0 || wk.im != 0.0) kernels |= kp ? BIE_KERNEL_KP : BIE_KERNEL_K;
   const NearOut o = {(cplx*)A_out, s->N, 0, 0};
   return near_stage(ctx, s, kernels, k, ws, wk, unweighted ? s->jac : nullptr, o, nullptr);
 }

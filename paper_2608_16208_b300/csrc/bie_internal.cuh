@@ -5,7 +5,7 @@
 //   * cancellation-free differences r(v) - r(u) by the straight-path line
 //     integral of the first derivatives (Section 4, Remark), 16-point
 //     Gauss-Legendre
-//   * warp-cooperative mixed-radix (4, 2, 3) Stockham FFT in shared memory
+//   * warp-cooperative mixed-radix (4, 2, 3, 5) Stockham FFT in shared memory
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -66,12 +66,22 @@ __device__ __forceinline__ cplx shfl(cplx v, int src) {
 }
 
 // ------------------------------------------------------------------ surfaces
+// 16-point Gauss-Legendre on [0, 1] (nodes and weights), filled by the host.
+struct GL16 {
+  double x[16], w[16];
+};
+
 struct SurfP {
-  int kind;       // 0 ellipsoid, 1 star
-  int nt;         // number of star terms
+  int kind;       // 0 ellipsoid, 1 star, 2 bean, 3 torus, 4 Fourier torus
+  int nt;         // number of star / Fourier-torus terms
+  int periodic;   // t-periodic (tori): the first and last panels are neighbours
+  double L;       // parameter length of the generating curve (pi, or 2 pi for tori)
   double ax, ay, az;
+  double R, eps;  // tori: R; the wiggly torus's eps and m (mm)
+  int mm;
   double c[BIE_MAX_TERMS];
-  int8_t p[BIE_MAX_TERMS], q[BIE_MAX_TERMS], m[BIE_MAX_TERMS], s[BIE_MAX_TERMS];
+  int8_t p[BIE_MAX_TERMS], q[BIE_MAX_TERMS], m[BIE_MAX_TERMS], s[BIE_MAX_TERMS];   // Fourier torus: m, n in m, q
+  GL16 gl;        // Gauss-Legendre on [0, 1] for the line-integral differences of kinds 2-4
 };
 
 template <typename T>
@@ -132,6 +142,72 @@ static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double t
     }
     return;
   }
+  if (S.kind == 2) {   // bean: r = (f_A(t) cos th, y0(t) + f_B(t) sin th, cos t)
+    const double u = cos(kPi * ct), su = sin(kPi * ct);
+    const double du = kPi * st * su, ddu = kPi * ct * su - (kPi * st) * (kPi * st) * u;
+    double fa[3], fb[3];
+    for (int which = 0; which < 2; ++which) {
+      const double c0 = which ? 0.4 : 0.1;
+      const double g = 1 - c0 * u, sg = sqrt(g), dg = -c0 * du, ddg = -c0 * ddu;
+      const double dsg = dg / (2 * sg), ddsg = ddg / (2 * sg) - dg * dg / (4 * g * sg);
+      double* f = which ? fb : fa;
+      f[0] = 0.8 * sg * st;
+      f[1] = 0.8 * (dsg * st + sg * ct);
+      f[2] = 0.8 * (ddsg * st + 2 * dsg * ct - sg * st);
+    }
+    const double y0 = -0.3 * u, y0t = -0.3 * du, y0tt = -0.3 * ddu;
+    g->r = {fa[0] * cp, y0 + fb[0] * sp, ct};
+    if (order >= 1) {
+      g->rt = {fa[1] * cp, y0t + fb[1] * sp, -st};
+      g->rth = {-fa[0] * sp, fb[0] * cp, 0.0};
+    }
+    if (order >= 2) {
+      g->rtt = {fa[2] * cp, y0tt + fb[2] * sp, -ct};
+      g->rtth = {-fa[1] * sp, fb[1] * cp, 0.0};
+      g->rthth = {-fa[0] * cp, -fb[0] * sp, 0.0};
+    }
+    return;
+  }
+  if (S.kind == 3) {   // torus: r = (a w cos t, b w sin t, c sin th), w = R + cos th + eps cos(m t)
+    double smt, cmt;
+    sincos(S.mm * t, &smt, &cmt);
+    const double w = S.R + cp + S.eps * cmt, wt = -S.eps * S.mm * smt, wth = -sp;
+    const double wtt = -S.eps * S.mm * S.mm * cmt, wthth = -cp;
+    g->r = {S.ax * w * ct, S.ay * w * st, S.az * sp};
+    if (order >= 1) {
+      g->rt = {S.ax * (wt * ct - w * st), S.ay * (wt * st + w * ct), 0.0};
+      g->rth = {S.ax * wth * ct, S.ay * wth * st, S.az * cp};
+    }
+    if (order >= 2) {
+      g->rtt = {S.ax * (wtt * ct - 2 * wt * st - w * ct), S.ay * (wtt * st + 2 * wt * ct - w * st), 0.0};
+      g->rtth = {-S.ax * wth * st, S.ay * wth * ct, 0.0};
+      g->rthth = {S.ax * wthth * ct, S.ay * wthth * st, -S.az * sp};
+    }
+    return;
+  }
+  if (S.kind == 4) {   // Fourier torus: r = (w cos t, w sin t, zeta), w = R + sum c cos(m th + n t), zeta = sum c sin(.)
+    double w = S.R, wt = 0, wth = 0, wtt = 0, wtth = 0, wthth = 0, z = 0, zt = 0, zh = 0, ztt = 0, zth = 0, zhh = 0;
+    for (int i = 0; i < S.nt; ++i) {
+      const double mm = S.m[i], nn = S.q[i], c = S.c[i];
+      double sph, cph;
+      sincos(mm * th + nn * t, &sph, &cph);
+      w += c * cph; wt -= c * nn * sph; wth -= c * mm * sph;
+      wtt -= c * nn * nn * cph; wtth -= c * mm * nn * cph; wthth -= c * mm * mm * cph;
+      z += c * sph; zt += c * nn * cph; zh += c * mm * cph;
+      ztt -= c * nn * nn * sph; zth -= c * mm * nn * sph; zhh -= c * mm * mm * sph;
+    }
+    g->r = {w * ct, w * st, z};
+    if (order >= 1) {
+      g->rt = {wt * ct - w * st, wt * st + w * ct, zt};
+      g->rth = {wth * ct, wth * st, zh};
+    }
+    if (order >= 2) {
+      g->rtt = {wtt * ct - 2 * wt * st - w * ct, wtt * st + 2 * wt * ct - w * st, ztt};
+      g->rtth = {wtth * ct - wth * st, wtth * st + wth * ct, zth};
+      g->rthth = {wthth * ct, wthth * st, zhh};
+    }
+    return;
+  }
   double h = 1.0, ht = 0.0, hth = 0.0, htt = 0.0, htth = 0.0, hthth = 0.0;
   for (int i = 0; i < S.nt; ++i) {
     double gg, gt, gtt, sm, cm;
@@ -184,6 +260,45 @@ static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx t
     *rth = {-S.ax * st * sp, S.ay * st * cp, C(0.0)};
     return;
   }
+  if (S.kind == 2) {   // bean (t real: every factor of t is real)
+    const double u = cos(kPi * ct), su = sin(kPi * ct), du = kPi * st * su;
+    double fa0, fa1, fb0, fb1;
+    for (int which = 0; which < 2; ++which) {
+      const double c0 = which ? 0.4 : 0.1;
+      const double g = 1 - c0 * u, sg = sqrt(g), dsg = -c0 * du / (2 * sg);
+      (which ? fb0 : fa0) = 0.8 * sg * st;
+      (which ? fb1 : fa1) = 0.8 * (dsg * st + sg * ct);
+    }
+    *r = {fa0 * cp, C(-0.3 * u) + fb0 * sp, C(ct)};
+    *rt = {fa1 * cp, C(-0.3 * du) + fb1 * sp, C(-st)};
+    *rth = {-fa0 * sp, fb0 * cp, C(0.0)};
+    return;
+  }
+  if (S.kind == 3) {   // torus
+    double smt, cmt;
+    sincos(S.mm * t, &smt, &cmt);
+    const cplx w = C(S.R + S.eps * cmt) + cp;
+    const double wt = -S.eps * S.mm * smt;
+    const cplx wth = -sp;
+    *r = {(S.ax * ct) * w, (S.ay * st) * w, S.az * sp};
+    *rt = {S.ax * (C(wt * ct) - st * w), S.ay * (C(wt * st) + ct * w), C(0.0)};
+    *rth = {(S.ax * ct) * wth, (S.ay * st) * wth, S.az * cp};
+    return;
+  }
+  if (S.kind == 4) {   // Fourier torus
+    cplx w = C(S.R), wt = C(0.0), wth = C(0.0), z = C(0.0), zt = C(0.0), zh = C(0.0);
+    for (int i = 0; i < S.nt; ++i) {
+      const double mm = S.m[i], nn = S.q[i], c = S.c[i];
+      cplx cph, sph;
+      ccossin(mm * th + C(nn * t), &cph, &sph);
+      w = w + c * cph; wt = wt - (c * nn) * sph; wth = wth - (c * mm) * sph;
+      z = z + c * sph; zt = zt + (c * nn) * cph; zh = zh + (c * mm) * cph;
+    }
+    *r = {ct * w, st * w, z};
+    *rt = {ct * wt - st * w, st * wt + ct * w, zt};
+    *rth = {ct * wth, st * wth, zh};
+    return;
+  }
   cplx h = C(1.0), ht = C(0.0), hth = C(0.0);
   for (int i = 0; i < S.nt; ++i) {
     double gg, gt, gtt;
@@ -208,11 +323,6 @@ static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx t
   *rt = {ht * e.x + h * et.x, ht * e.y + h * et.y, ht * e.z + h * et.z};
   *rth = {hth * e.x + h * eth.x, hth * e.y + h * eth.y, hth * e.z + h * eth.z};
 }
-
-// 16-point Gauss-Legendre on [0, 1] (nodes and weights), filled by the host.
-struct GL16 {
-  double x[16], w[16];
-};
 
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251436;
 __device__ __forceinline__ double wrap_pi(double d) { return d - kTwoPi * rint(d * kInvTwoPi); }
@@ -251,6 +361,7 @@ __host__ __device__ inline FFTPlan make_plan(int n) {
   while (m % 4 == 0) { p.rad[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.rad[p.nst++] = 2; m /= 2; }
   while (m % 3 == 0) { p.rad[p.nst++] = 3; m /= 3; }
+  while (m % 5 == 0) { p.rad[p.nst++] = 5; m /= 5; }
   if (m != 1) p.nst = -1;
   return p;
 }
@@ -271,7 +382,7 @@ static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cpl
     const int tstep = (T / n) * (n / (Ns * R));  // table index step per (r * jm)
     for (int j = lane; j < stride; j += 32) {
       const int jm = j % Ns;
-      cplx v[4];
+      cplx v[5];
       for (int r = 0; r < R; ++r) {
         cplx a = src[j + r * stride];
         if (r && jm) {
@@ -281,8 +392,20 @@ static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cpl
         }
         v[r] = a;
       }
-      cplx o[4];
-      if (R == 4) {
+      cplx o[5];
+      if (R == 5) {
+        // DFT of length 5: cos and sin of 2 pi / 5 and 4 pi / 5
+        const double c1 = 0.30901699437494742, c2 = -0.80901699437494742;
+        const double s1 = 0.95105651629515357 * sign, s2 = 0.58778525229247313 * sign;
+        const cplx t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
+        const cplx a1 = v[0] + c1 * t1 + c2 * t2, a2 = v[0] + c2 * t1 + c1 * t2;
+        const cplx b1 = s1 * t3 + s2 * t4, b2 = s2 * t3 - s1 * t4;   // times i below
+        o[0] = v[0] + t1 + t2;
+        o[1] = a1 + C(-b1.im, b1.re);
+        o[4] = a1 - C(-b1.im, b1.re);
+        o[2] = a2 + C(-b2.im, b2.re);
+        o[3] = a2 - C(-b2.im, b2.re);
+      } else if (R == 4) {
         cplx s02 = v[0] + v[2], d02 = v[0] - v[2], s13 = v[1] + v[3], d13 = v[1] - v[3];
         cplx jd = sign < 0 ? C(d13.im, -d13.re) : C(-d13.im, d13.re);  // sign*i*d13
         o[0] = s02 + s13;

@@ -158,7 +158,7 @@ __device__ __forceinline__ void dw_sincos(double x, float2* sn, float2* cs) {
 }
 
 // ------------------------------------------------------------------ warp FFT
-// Same transform and buffer contract as warp_fft (Stockham, radices 4, 2, 3; the result lands in
+// Same transform and buffer contract as warp_fft (Stockham, radices 4, 2, 3, 5; the result lands in
 // x or y, returned), on double-word complex values; tw: the twiddle table e^{-2 pi i k / T} in
 // double-word form.
 __device__ __forceinline__ float4 tw_load(const float4* __restrict__ tw, int idx, int sign) {
@@ -217,6 +217,35 @@ static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, 
         const int idx = ix.quo(j) * Ns * 2 + jm;
         dst[idx] = dwc_add(v0, v1);
         dst[idx + Ns] = dwc_sub(v0, v1);
+      }
+    } else if (R == 5) {
+      // cos and sin of 2 pi / 5 and 4 pi / 5 as double words (the sines carry the sign)
+      const float2 c1 = make_float2(0.30901700258255005f, -8.207602597565256e-09f);
+      const float2 c2 = make_float2(-0.80901700258255f, 8.207602597565256e-09f);
+      const float2 s1 = make_float2(sign * 0.9510565400123596f, sign * -2.3717205976936384e-08f);
+      const float2 s2 = make_float2(sign * 0.5877852439880371f, sign * 8.304436249773062e-09f);
+      for (int j = lane; j < stride; j += 32) {
+        const int jm = ix.rem(j);
+        const float4 v0 = src[j];
+        float4 v1 = src[j + stride], v2 = src[j + 2 * stride], v3 = src[j + 3 * stride], v4 = src[j + 4 * stride];
+        if (jm) {
+          v1 = dwc_mul(v1, tw_load(tw, jm * tstep, sign));
+          v2 = dwc_mul(v2, tw_load(tw, 2 * jm * tstep, sign));
+          v3 = dwc_mul(v3, tw_load(tw, 3 * jm * tstep, sign));
+          v4 = dwc_mul(v4, tw_load(tw, 4 * jm * tstep, sign));
+        }
+        const float4 t1 = dwc_add(v1, v4), t2 = dwc_add(v2, v3), t3 = dwc_sub(v1, v4), t4 = dwc_sub(v2, v3);
+        const float4 a1 = dwc_add(v0, dwc_add(dwc_mulr(t1, c1), dwc_mulr(t2, c2)));
+        const float4 a2 = dwc_add(v0, dwc_add(dwc_mulr(t1, c2), dwc_mulr(t2, c1)));
+        const float4 b1 = dwc_add(dwc_mulr(t3, s1), dwc_mulr(t4, s2));
+        const float4 b2 = dwc_sub(dwc_mulr(t3, s2), dwc_mulr(t4, s1));
+        const float4 ib1 = make_float4(-b1.z, -b1.w, b1.x, b1.y), ib2 = make_float4(-b2.z, -b2.w, b2.x, b2.y);
+        const int idx = ix.quo(j) * Ns * 5 + jm;
+        dst[idx] = dwc_add(v0, dwc_add(t1, t2));
+        dst[idx + Ns] = dwc_add(a1, ib1);
+        dst[idx + 2 * Ns] = dwc_add(a2, ib2);
+        dst[idx + 3 * Ns] = dwc_sub(a2, ib2);
+        dst[idx + 4 * Ns] = dwc_sub(a1, ib1);
       }
     } else {
       for (int j = lane; j < stride; j += 32) {

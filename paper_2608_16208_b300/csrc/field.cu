@@ -8,20 +8,26 @@
 
 namespace bie {
 
-__global__ void rhs_kernel(int64_t N, const double* __restrict__ pts, int kind, double px, double py, double pz,
-                           double k, double2* __restrict__ g) {
+__global__ void rhs_kernel(int64_t N, const double* __restrict__ pts, const double* __restrict__ nrm, int kind,
+                           double px, double py, double pz, double k, double2* __restrict__ g) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
     double s, c;
     if (kind == 0) {  // sound-soft plane wave: -e^{ik d.x}
       sincos(k * (px * x + py * y + pz * z), &s, &c);
       g[i] = make_double2(-c, -s);
-    } else {          // point source e^{ik r}/(4 pi r)
+    } else {
       const double dx = x - px, dy = y - py, dz = z - pz;
       const double r = sqrt(dx * dx + dy * dy + dz * dz);
       sincos(k * r, &s, &c);
       const double f = 1.0 / (4 * kPi * r);
-      g[i] = make_double2(c * f, s * f);
+      if (kind == 1) {   // point source e^{ik r}/(4 pi r)
+        g[i] = make_double2(c * f, s * f);
+      } else {           // its normal derivative nu.(x - src) e^{ik r} (ik r - 1) / (4 pi r^3)
+        const double nd = (nrm[3 * i] * dx + nrm[3 * i + 1] * dy + nrm[3 * i + 2] * dz) * f / (r * r);
+        // e^{ikr} (ikr - 1) = (-cos - kr sin) + i (kr cos - sin)
+        g[i] = make_double2(nd * (-c - k * r * s), nd * (k * r * c - s));
+      }
     }
   }
 }
@@ -141,8 +147,9 @@ using namespace bie;
 extern "C" {
 
 bie_status bie_rhs(bie_ctx ctx, bie_surface s, int kind, const double* param, double k, double* g) {
-  if (!ctx || !s || !param || !g || (kind != 0 && kind != 1)) { set_error("bie_rhs: invalid arguments"); return BIE_EINVAL; }
-  rhs_kernel<<<ctx->sms * 4, 256, 0, ctx->stream>>>(s->N, s->pts, kind, param[0], param[1], param[2], k, (double2*)g);
+  if (!ctx || !s || !param || !g || kind < 0 || kind > 2) { set_error("bie_rhs: invalid arguments"); return BIE_EINVAL; }
+  rhs_kernel<<<ctx->sms * 4, 256, 0, ctx->stream>>>(s->N, s->pts, s->nrm, kind, param[0], param[1], param[2], k,
+                                                    (double2*)g);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BIE_OK : cuda_fail(e, "rhs_kernel");
 }

@@ -8,12 +8,15 @@ struct PairArgs {
   SurfP S;
   GL16 gl;
   int Np, Mt, M, P, T, L;         // P: Toeplitz transform length; L: highest A_m index
-  int kernels;                    // BIE_KERNEL_S | BIE_KERNEL_K
+  int kernels;                    // BIE_KERNEL_S and at most one of BIE_KERNEL_K, BIE_KERNEL_KP
+  int kprime;                     // the double layer of this launch is K' (tau_0 with the target's normal)
+  int out_nk, out_k0;             // modes_out holds out_nk kernels per pair; this launch writes from slot out_k0
   double h, k;
   int64_t N, n_pairs, p0;         // p0: first enumerated pair of this launch
   int enumerate;                  // 1: pair p enumerates every (node, delta, g, theta) of the surface
   const double* t_nodes;
   const double* pts;
+  const double* nrm;              // unit normals of the nodes (the target's normal of K')
   const double* ring_t;
   const double* ring_r;
   const double* ring_n;

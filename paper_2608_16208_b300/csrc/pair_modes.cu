@@ -66,9 +66,41 @@ __device__ __forceinline__ double ipow(double x, int n) {
   return r;
 }
 
+// r(t_s, ths) - r(t, th) by the line integral of the first derivatives along the straight parameter
+// path (Section 4, Remark), 16-point Gauss-Legendre: the cancellation-free difference of the surface
+// kinds without a closed form below (bean, tori); ths real or complex.
+__device__ __forceinline__ void first_derivs(const SurfP& S, double t, double th, R3* rt, R3* rth) {
+  Geo G;
+  surf_eval(S, t, th, 1, &G);
+  *rt = G.rt;
+  *rth = G.rth;
+}
+__device__ __forceinline__ void first_derivs(const SurfP& S, double t, cplx th, C3* rt, C3* rth) {
+  C3 r;
+  surf_eval_c(S, t, th, &r, rt, rth);
+}
+__device__ __forceinline__ double wrapped_dth(double th, double ths) { return wrap_pi(th - ths); }
+__device__ __forceinline__ cplx wrapped_dth(double th, cplx ths) { return C(wrap_pi(th - ths.re), -ths.im); }
+template <typename T>
+__device__ __noinline__ V3<T> diff_path(const SurfP& S, double ts, T ths, double t, double th) {
+  const double dt = t - ts;
+  const T dth = wrapped_dth(th, ths);
+  V3<T> acc = {mk<T>(0.0), mk<T>(0.0), mk<T>(0.0)};
+  for (int j = 0; j < 16; ++j) {
+    const double lam = S.gl.x[j], w = S.gl.w[j];
+    V3<T> rt, rth;
+    first_derivs(S, ts + lam * dt, ths + lam * dth, &rt, &rth);
+    acc.x = acc.x + w * (dt * rt.x + rth.x * dth);
+    acc.y = acc.y + w * (dt * rt.y + rth.y * dth);
+    acc.z = acc.z + w * (dt * rt.z + rth.z * dth);
+  }
+  return {-1.0 * acc.x, -1.0 * acc.y, -1.0 * acc.z};
+}
+
 // r(t_s, ths) - r(t, th) without cancellation (sum-to-product identities); ths real or complex.
 template <typename T>
 __device__ __noinline__ V3<T> diff_ana(const SurfP& S, double ts, T ths, double t, double th) {
+  if (S.kind >= 2) return diff_path<T>(S, ts, ths, t, th);
   double s1, c1, s0, c0, smt, cmt;
   sincos(ts, &s1, &c1);
   sincos(t, &s0, &c0);
@@ -627,8 +659,8 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
       }
       PairInfo pr = {};
       const int64_t tn = row / Mt;
-      const int ip = (int)(tn / 16) + d - 1;
-      pr.valid = !(row < 0 || row >= a.N || d < 0 || ip < 0 || ip >= a.Np);
+      const int ip = (int)(tn / 16) + d - 1;   // on a torus every panel has both neighbours
+      pr.valid = !(row < 0 || row >= a.N || d < 0 || (!a.S.periodic && (ip < 0 || ip >= a.Np)));
       pr.row = row;
       if (pr.valid) {
         pr.ring = (tn * 3 + d) * 16 + g;
@@ -735,7 +767,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(isS ? sm.sn[q] : sm.bt0[q], 0.0);
         __syncwarp();
         const cplx* Sf = warp_fft_x(sm.W0, sm.W1, Mt, a.twf, a.T, -1);
-        double* out = a.modes_out + (p * nk + kidx) * 2 * (Mt + 1);
+        double* out = a.modes_out + (p * a.out_nk + a.out_k0 + kidx) * 2 * (Mt + 1);
         for (int mm = lane; mm <= 2 * M; mm += 32) {
           const int m = mm - M;
           cplx sv = Sf[wrapi(m, Mt)] * (1.0 / Mt);
@@ -767,7 +799,8 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       const int64_t p = a.out_mod ? (a.out_base + p0 + pi) % a.out_mod : p0 + pi;   // output slot
       if (!pr.valid) {
         if (a.modes_out)
-          for (int m = lane; m < 2 * nk * (Mt + 1); m += 32) a.modes_out[p * 2 * nk * (Mt + 1) + m] = 0.0;
+          for (int m = lane; m < 2 * nk * (Mt + 1); m += 32)
+            a.modes_out[(p * a.out_nk + a.out_k0) * 2 * (Mt + 1) + m] = 0.0;
         if (a.weights_out)
           for (int kk = 0; kk < nk; ++kk)
             for (int m = lane; m < Mt; m += 32) a.weights_out[kk * a.weights_stride + p * a.w_ld + m] = C(0.0);
@@ -810,6 +843,8 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       // ---- D3. samples
       double sha, cha;   // sin(a/2), cos(a/2)
       sincos(0.5 * ra, &sha, &cha);
+      const double nux = a.kprime ? a.nrm[3 * pr.row] : 0.0, nuy = a.kprime ? a.nrm[3 * pr.row + 1] : 0.0,
+                   nuz = a.kprime ? a.nrm[3 * pr.row + 2] : 0.0;
       for (int w = lane; w < (Mt + 31) / 32; w += 32) sm.nearbits[w] = 0u;
       __syncwarp();
       for (int q = lane; q < Mt; q += 32) {
@@ -854,7 +889,9 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           al = (1 - ckr - x * skr) / r2;
           be = (skr - x * ckr) / (r2 * rho);
         }
-        sm.tau0[q] = rn[3 * q] * yx + rn[3 * q + 1] * yy + rn[3 * q + 2] * yz;   // near ones replaced below
+        // tau_0 = nu(y) . (y - x) (K: the source normal) or nu(x) . (x - y) (K': the target's normal);
+        // near ones are replaced below
+        sm.tau0[q] = a.kprime ? -(nux * yx + nuy * yy + nuz * yz) : rn[3 * q] * yx + rn[3 * q + 1] * yy + rn[3 * q + 2] * yz;
         sm.alph[q] = al;
         sm.bt0[q] = be;
         sm.hr[q] = F;
@@ -877,14 +914,21 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           const double dth = wrap_pi(pr.th - thq);
           double acc = 0.0;
           if (nearq) {
+            // int_0^1 (lam - 1) nu(v) . D^2 r(v + lam d)[d, d] dlam from the point v whose normal enters:
+            // the source (K) or the target (K')
             const int jn = lane & 15;
-            const double dt = pr.t - pr.ts, lam = a.gl.x[jn];
+            const double lam = a.gl.x[jn];
+            const double dt = a.kprime ? pr.ts - pr.t : pr.t - pr.ts;
+            const double dd = a.kprime ? -dth : dth;
+            const double tv = a.kprime ? pr.t : pr.ts, thv = a.kprime ? pr.th : thq;
+            const double vx = a.kprime ? nux : rn[3 * q], vy = a.kprime ? nuy : rn[3 * q + 1],
+                         vz = a.kprime ? nuz : rn[3 * q + 2];
             Geo G;
-            surf_eval(a.S, pr.ts + lam * dt, thq + lam * dth, 2, &G);
-            const double qx = G.rtt.x * dt * dt + 2 * G.rtth.x * dt * dth + G.rthth.x * dth * dth;
-            const double qy = G.rtt.y * dt * dt + 2 * G.rtth.y * dt * dth + G.rthth.y * dth * dth;
-            const double qz = G.rtt.z * dt * dt + 2 * G.rtth.z * dt * dth + G.rthth.z * dth * dth;
-            acc = a.gl.w[jn] * (lam - 1) * (rn[3 * q] * qx + rn[3 * q + 1] * qy + rn[3 * q + 2] * qz);
+            surf_eval(a.S, tv + lam * dt, thv + lam * dd, 2, &G);
+            const double qx = G.rtt.x * dt * dt + 2 * G.rtth.x * dt * dd + G.rthth.x * dd * dd;
+            const double qy = G.rtt.y * dt * dt + 2 * G.rtth.y * dt * dd + G.rthth.y * dd * dd;
+            const double qz = G.rtt.z * dt * dt + 2 * G.rtth.z * dt * dd + G.rthth.z * dd * dd;
+            acc = a.gl.w[jn] * (lam - 1) * (vx * qx + vy * qy + vz * qz);
           }
           for (int o = 8; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
           if (nearq && (lane & 15) == 0) sm.tau0[q] = acc;
@@ -964,23 +1008,30 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         const R3 dn = {dn1.x + dn2.x, dn1.y + dn2.y, dn1.z + dn2.z};
         const double nd = dot(nu, dn);
         const R3 dnu = {(dn.x - nu.x * nd) / J, (dn.y - nu.y * nd) / J, (dn.z - nu.z * nd) / J};
-        double t0a = dot(nu, Y);
+        // K: tau_0(a) = nu(a) . Y, tau_0'(a) = nu'(a) . Y (+ nu . r_th = 0);
+        // K': tau_0(a) = -nu(x) . Y, tau_0'(a) = -nu(x) . r_th(t_s, a)
+        const R3 nux3 = {nux, nuy, nuz};
+        double t0a = a.kprime ? -dot(nux3, Y) : dot(nu, Y);
         if (neara) {
           double acc = 0.0;
           if (lane < 16) {
-            const double dt = pr.t - pr.ts, dth = wrap_pi(pr.th - ra), lam = a.gl.x[lane];
+            const double lam = a.gl.x[lane];
+            const double dt = a.kprime ? pr.ts - pr.t : pr.t - pr.ts;
+            const double dth = a.kprime ? wrap_pi(ra - pr.th) : wrap_pi(pr.th - ra);
+            const double tv = a.kprime ? pr.t : pr.ts, thv = a.kprime ? pr.th : ra;
+            const R3 nv = a.kprime ? nux3 : nu;
             Geo H;
-            surf_eval(a.S, pr.ts + lam * dt, ra + lam * dth, 2, &H);
+            surf_eval(a.S, tv + lam * dt, thv + lam * dth, 2, &H);
             const double qx = H.rtt.x * dt * dt + 2 * H.rtth.x * dt * dth + H.rthth.x * dth * dth;
             const double qy = H.rtt.y * dt * dt + 2 * H.rtth.y * dt * dth + H.rthth.y * dth * dth;
             const double qz = H.rtt.z * dt * dt + 2 * H.rtth.z * dt * dth + H.rthth.z * dth * dth;
-            acc = a.gl.w[lane] * (lam - 1) * (nu.x * qx + nu.y * qy + nu.z * qz);
+            acc = a.gl.w[lane] * (lam - 1) * (nv.x * qx + nv.y * qy + nv.z * qz);
           }
           t0a = warp_sum(acc);
         }
         const double r2a = dot(Y, Y);
         const double Fa = om / sqrt(r2a);
-        const double dt0 = dot(dnu, Y);
+        const double dt0 = a.kprime ? -dot(nux3, G.rth) : dot(dnu, Y);
         H3a = t0a * Fa * Fa * Fa;
         H3pa = dt0 * Fa * Fa * Fa + 3 * t0a * Fa * Fa * dFa;
         // ---- D8. remainder R on the grid (stable sum within kNearPhi of a); modes d_k
@@ -1176,7 +1227,10 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.Mt = s->Mt;
   a.M = s->Mt / 2;
   a.kernels = (int)kernels;
-  const bool withK = kernels & BIE_KERNEL_K;
+  const bool withK = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
+  a.kprime = (kernels & BIE_KERNEL_KP) ? 1 : 0;
+  a.out_nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + (withK ? 1 : 0);
+  a.out_k0 = 0;
   a.P = (withK ? 4 : 3) * s->Mt;
   a.L = (withK ? 4 : 3) * a.M;
   a.T = s->tw_len;
@@ -1185,6 +1239,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.N = s->N;
   a.t_nodes = s->t_nodes;
   a.pts = s->pts;
+  a.nrm = s->nrm;
   a.ring_t = s->ring_t;
   a.ring_r = s->ring_r;
   a.ring_n = s->ring_n;
@@ -1198,7 +1253,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
 
 int pair_warps_per_block(int Mt, unsigned kernels) {
   // the CTA shape (1, 2 or 4 warps) with the most resident warps per SM
-  const bool withK = kernels & BIE_KERNEL_K;
+  const bool withK = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
   const int P = (withK ? 4 : 3) * Mt, L = (withK ? 4 : 3) * (Mt / 2);
   const size_t per = smem_doubles(Mt, P, L, withK) * sizeof(double);
   auto kern = withK ? pair_kernel<true> : pair_kernel<false>;
@@ -1287,7 +1342,7 @@ static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
 }
 
 bie_status launch_pairs(bie_surface s, PairArgs& a) {
-  const bool withK = a.kernels & BIE_KERNEL_K;
+  const bool withK = a.kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
   if (!withK) return launch_pairs_split(s, a);
   const int wpb = pair_warps_per_block(a.Mt, (unsigned)a.kernels);
   if (wpb < 1) { set_error("pair kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
@@ -1333,17 +1388,30 @@ extern "C" bie_status bie_kernel_modes(bie_ctx ctx, bie_surface s, unsigned kern
     return BIE_EINVAL;
   }
   if (!(k > 0) || !(k < 1e6)) { set_error("bie_kernel_modes: k must be in (0, 1e6)"); return BIE_EINVAL; }
-  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) {
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K | BIE_KERNEL_KP))) {
     set_error("bie_kernel_modes: bad kernel mask %u", kernels);
     return BIE_EINVAL;
   }
   if (n_pairs == 0) return BIE_OK;
-  PairArgs a = make_pair_args(s, k, kernels);
+  // one launch per double-layer kind: (S and) K or K' first, then K' alone when both are asked
+  const int total = __builtin_popcount(kernels);
+  const unsigned first = (kernels & BIE_KERNEL_S) | ((kernels & BIE_KERNEL_K) ? BIE_KERNEL_K : (kernels & BIE_KERNEL_KP));
+  PairArgs a = make_pair_args(s, k, first);
   a.rows = pair_row;
   a.srcs = pair_src;
   a.n_pairs = n_pairs;
   a.modes_out = modes_out;
-  return launch_pairs(s, a);
+  a.out_nk = total;
+  bie_status st = launch_pairs(s, a);
+  if (st != BIE_OK || first == kernels) return st;
+  PairArgs b = make_pair_args(s, k, BIE_KERNEL_KP);
+  b.rows = pair_row;
+  b.srcs = pair_src;
+  b.n_pairs = n_pairs;
+  b.modes_out = modes_out;
+  b.out_nk = total;
+  b.out_k0 = total - 1;
+  return launch_pairs(s, b);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -1546,11 +1614,15 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     set_error("bie_batch_create: invalid arguments");
     return BIE_EINVAL;
   }
-  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K))) { set_error("bie_batch_create: bad kernel mask"); return BIE_EINVAL; }
+  if (kernels == 0 || (kernels & ~(BIE_KERNEL_S | BIE_KERNEL_K | BIE_KERNEL_KP)) ||
+      ((kernels & BIE_KERNEL_K) && (kernels & BIE_KERNEL_KP))) {
+    set_error("bie_batch_create: bad kernel mask (S and at most one of K, KP)");
+    return BIE_EINVAL;
+  }
   bie_batch_s* b = new bie_batch_s();
   b->ctx = ctx;
   b->kernels = kernels;
-  b->withK = kernels & BIE_KERNEL_K;
+  b->withK = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
   b->n_surf = n_surf;
   b->maxMt = 0;
   for (int i = 0; i < n_surf; ++i) {

@@ -49,6 +49,7 @@ static bool valid_length(int Mt) {
   int m = Mt;
   while (m % 2 == 0) m /= 2;
   while (m % 3 == 0) m /= 3;
+  while (m % 5 == 0) m /= 5;
   return m == 1;
 }
 
@@ -62,18 +63,21 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
                               const bie_quad_tables* ggq, bie_surface* out) {
   if (!ctx || !desc || !ggq || !out) { set_error("bie_surface_sample: NULL argument"); return BIE_EINVAL; }
   if (Np < 2 || Np > 4096) { set_error("bie_surface_sample: n_panels %d out of [2, 4096]", Np); return BIE_EINVAL; }
-  if (!valid_length(Mt)) { set_error("bie_surface_sample: m_theta %d must be even, 2^a 3^b, in [8, 1024]", Mt); return BIE_EINVAL; }
-  if (desc->kind != 0 && desc->kind != 1) { set_error("bie_surface_sample: unknown kind %d", desc->kind); return BIE_EINVAL; }
-  if (desc->kind == 1 && (desc->n_terms < 0 || desc->n_terms > BIE_MAX_TERMS || (desc->n_terms && !desc->terms))) {
+  if (!valid_length(Mt)) { set_error("bie_surface_sample: m_theta %d must be even, 2^a 3^b 5^c, in [8, 1024]", Mt); return BIE_EINVAL; }
+  if (desc->kind < 0 || desc->kind > 4) { set_error("bie_surface_sample: unknown kind %d", desc->kind); return BIE_EINVAL; }
+  const bool with_terms = desc->kind == 1 || desc->kind == 3 || desc->kind == 4;
+  if (with_terms && (desc->n_terms < 0 || desc->n_terms > BIE_MAX_TERMS || (desc->n_terms && !desc->terms))) {
     set_error("bie_surface_sample: n_terms %d out of [0, %d]", desc->n_terms, BIE_MAX_TERMS);
     return BIE_EINVAL;
   }
+  if (desc->kind == 3 && desc->n_terms != 1) { set_error("bie_surface_sample: the torus takes one term (R, eps, m)"); return BIE_EINVAL; }
+  const bool periodic = desc->kind == 3 || desc->kind == 4;
+  if (periodic && Np < 3) { set_error("bie_surface_sample: a torus needs n_panels >= 3"); return BIE_EINVAL; }
   {
     // non-finite descriptor values or tables would sample NaN geometry: refuse them here
     bool finite = true;
-    if (desc->kind == 0)
-      for (int c = 0; c < 3; ++c) finite = finite && std::isfinite(desc->axes[c]);
-    else
+    for (int c = 0; c < 3; ++c) finite = finite && std::isfinite(desc->axes[c]);
+    if (with_terms)
       for (int i = 0; i < 5 * desc->n_terms; ++i) finite = finite && std::isfinite(desc->terms[i]);
     for (int i = 0; i < 3 * 16 * 16; ++i)
       finite = finite && std::isfinite((&ggq->x[0][0][0])[i]) && std::isfinite((&ggq->w[0][0][0])[i]);
@@ -88,6 +92,25 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   s->ctx = ctx;
   s->sp.kind = desc->kind;
   s->sp.ax = desc->axes[0]; s->sp.ay = desc->axes[1]; s->sp.az = desc->axes[2];
+  s->sp.periodic = periodic ? 1 : 0;
+  s->sp.L = periodic ? 2 * kPi : kPi;
+  if (desc->kind == 3) {
+    s->sp.R = desc->terms[0];
+    s->sp.eps = desc->terms[1];
+    s->sp.mm = (int)lrint(desc->terms[2]);
+    if (fabs(desc->terms[2]) > 100) { delete s; set_error("bie_surface_sample: torus m out of range"); return BIE_EINVAL; }
+  }
+  if (desc->kind == 4) {
+    s->sp.R = desc->axes[0];
+    s->sp.nt = desc->n_terms;
+    for (int i = 0; i < desc->n_terms; ++i) {
+      const double* tr = desc->terms + 5 * i;
+      if (fabs(tr[1]) > 100 || fabs(tr[2]) > 100) { delete s; set_error("bie_surface_sample: term %d out of range", i); return BIE_EINVAL; }
+      s->sp.c[i] = tr[0];
+      s->sp.m[i] = (int8_t)lrint(tr[1]);   // theta frequency
+      s->sp.q[i] = (int8_t)lrint(tr[2]);   // t frequency
+    }
+  }
   if (desc->kind == 1) {
     s->sp.nt = desc->n_terms;
     for (int i = 0; i < desc->n_terms; ++i) {
@@ -106,7 +129,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
   }
   s->Np = Np;
   s->Mt = Mt;
-  s->L = kPi;
+  s->L = s->sp.L;
   s->h = s->L / Np;
   s->N = (int64_t)16 * Np * Mt;
   s->n_rings = (int64_t)16 * Np * 48;
@@ -126,6 +149,7 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
       s->gl01.x[l] = (ggq->gl_x[l] + 1) / 2;
       s->gl01.w[l] = ggq->gl_w[l] / 2;
     }
+    s->sp.gl = s->gl01;
     if (fabs(wsum - 2.0) > 1e-13) {
       delete s;
       set_error("bie_surface_sample: Gauss-Legendre weights do not sum to 2");
@@ -139,9 +163,9 @@ bie_status bie_surface_sample(bie_ctx ctx, const bie_surface_desc* desc, int Np,
     for (int l = 0; l < 16; ++l)
       for (int d = 0; d < 3; ++d)
         for (int g = 0; g < 16; ++g) {
-          const int ip = j + d - 1;
+          const int ip = j + d - 1;   // past an end of a torus: the last / first panel, shifted by -L / +L
           const int64_t ring = (((int64_t)(j * 16 + l) * 3 + d) * 16 + g);
-          rt[ring] = (ip < 0 || ip >= Np) ? NAN : (ip + 0.5) * s->h + (s->h / 2) * ggq->x[d][l][g];
+          rt[ring] = (!periodic && (ip < 0 || ip >= Np)) ? NAN : (ip + 0.5) * s->h + (s->h / 2) * ggq->x[d][l][g];
         }
   // near-fill coefficients w_g L_n(x_g) (Lagrange basis on the 16 Legendre nodes)
   std::vector<double> coef(3 * 16 * 16 * 16);
@@ -238,7 +262,9 @@ void bie_surface_free(bie_surface s) {
 }
 
 int64_t bie_surface_unknowns(bie_surface s) { return s ? s->N : 0; }
-int64_t bie_surface_near_pairs(bie_surface s) { return s ? (int64_t)256 * s->Mt * (3 * s->Np - 2) : 0; }
+int64_t bie_surface_near_pairs(bie_surface s) {
+  return s ? (int64_t)256 * s->Mt * (3 * s->Np - (s->sp.periodic ? 0 : 2)) : 0;
+}
 const double* bie_surface_points(bie_surface s) { return s ? s->pts : nullptr; }
 const double* bie_surface_normals(bie_surface s) { return s ? s->nrm : nullptr; }
 const double* bie_surface_jacobians(bie_surface s) { return s ? s->jac : nullptr; }
