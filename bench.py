@@ -54,11 +54,30 @@ def _hbm_peak():
         return 6400.0, "fallback"
 
 
-FP64_PEAK_GFLOPS = 1105.0   # measured FP64 FMA throughput of this B300 pool (profiles/fp64_peak_probe.md)
+def fp64_peak_gflops():
+    """FP64 throughput of this GPU measured now: cuBLAS DGEMM 4096^3 (2 n^3 flops), best of 3, CUDA
+    events.  MEASURED_PEAKS.json has no FP64 figure, and the pair pipeline's roofline is FP64."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best / 1000.0) / 1e9
+
+
 # DRAM bytes (read + write) per pair of the pair pipeline (root kernel + transform kernel: the kernel
 # modes plus the per-pair records between the two), from one ncu capture of 75,776 pairs of this
-# workload (profiles/pair_kernel_ellipsoid_np16_m128_k10.md); valid only for the kernel sources it was
-# taken on: the report carries it while the sources hash to the same value, and null otherwise.
+# workload; valid only for the kernel sources it was taken on: the report carries it while the
+# sources hash to the same value, and null otherwise.
 PAIR_TRAFFIC = {"bytes_per_pair": (10.782976e6 + 296.570624e6 + 246.056192e6 + 123.324416e6) / 75776,
                 "sources": "8ca135997c44e2ff"}
 
@@ -326,6 +345,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     sk_ms = e0.elapsed_time(e1)
     del modes_sk, rows_all, srcs_all, panel, keep
+    fp64_peak = fp64_peak_gflops()
     fl = algorithmic_flops_per_pair(Mt)
     traffic = (PAIR_TRAFFIC["bytes_per_pair"] * pk_pairs
                if pair_kernel_sources_hash() == PAIR_TRAFFIC["sources"] else None)
@@ -382,9 +402,11 @@ def run_gpu(args):
             "config": config_json(c, {"parallelism": "replicas" if world > 1 else "single"}),
             "clocks": cs,
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
-                         "kernel": "pair_root_kernel + pair_transform_kernel (S)", "peak_source": "measured FP64 FMA probe",
+            "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak, "unit": "GFLOP/s",
+                         "frac": achieved_gflops / fp64_peak, "traffic": traffic,
+                         "kernel": "pair_root_kernel + pair_transform_kernel (S)",
+                         "peak_source": "FP64 measured in this run: cuBLAS DGEMM 4096^3, best of 3 (the transforms "
+                                        "run on the FP32 pipe, so this is an FP64-equivalent fraction)",
                          "traffic_source": "ncu capture of 75,776 pairs, scaled to the %d pairs of a launch" % pk_pairs,
                          "launch_ms": pk_ms,
                          "flops_per_pair": fl, "step_gflops": step_gflops},
@@ -477,12 +499,21 @@ def run_solves(bie, ctx, surf, c, A=None):
 
 
 def run_batch(bie, ctx, count, stream):
-    """Uneven batch (harmonic stars, Np in 8..32, Mth in 64..256, k in [1, 20]) in one persistent,
-    graph-captured launch, against the same surfaces run one after the other."""
+    """Uneven batch (harmonic stars, Np in 8..32, Mth in 64..256, k in [1, 20]) replayed from a CUDA graph
+    (one class of equal grid size after another), against the same surfaces as single-surface plans run
+    one after the other.  Throughput mode: the Parseval weights go to a ring of 2^20 pair rows (the GGQ
+    fill and the right-hand sides are not part of this measurement)."""
     import torch
     stream = torch.cuda.Stream()              # graph capture needs a non-default stream
     ctx = bie.Context(stream)
-    specs = wl.batch_surfaces(seed=0, count=count)
+    all_specs = wl.batch_surfaces(seed=0, count=count)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    # sharding over ranks (one GPU each): the surfaces share no pairs, so each rank plans its own share
+    # (longest-processing-time by near pairs x log2 Mth) and nothing moves between ranks
+    costs = [16 * sp["Np"] * 48 * sp["Mt"] * np.log2(sp["Mt"]) for sp in all_specs]
+    owner, load = bie.shard_surfaces(costs, world)
+    specs = [sp for sp, o in zip(all_specs, owner) if o == rank]
     ggq = wl.load_ggq()
     surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
     ks = [sp["k"] for sp in specs]
@@ -493,36 +524,53 @@ def run_batch(bie, ctx, count, stream):
     plan = bie.Batch(ctx, surfs, ks, bie.KERNEL_S, W, slot)
     plan.run()
     torch.cuda.synchronize()
+    plan_pairs, plan_config, plan_keep = plan.pairs, plan.config, plan
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         plan.run()
     torch.cuda.synchronize()
-    times = []
-    for _ in range(2):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):       # replay() launches on the current stream
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    ms = min(times)
-    # the same surfaces, one plan (one launch) each, back to back
-    singles = [bie.Batch(ctx, [sf], [k], bie.KERNEL_S, W, slot) for sf, k in zip(surfs, ks)]
-    for sp in singles:
-        sp.run()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for sp in singles:
-        sp.run()
-    e1.record(stream)
+    with torch.cuda.stream(stream):           # replay() launches on the current stream
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
     torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1)
-    return {"surfaces": count, "pairs": plan.pairs, "pairs_per_s": plan.pairs / (ms / 1000.0), "ms": ms,
-            "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms, "autotuned": plan.config,
-            "m_theta": sorted(sp["Mt"] for sp in specs), "panels": sorted(sp["Np"] for sp in specs),
-            "output": "ring of %d pairs x %d angles (throughput mode)" % (slot, maxMt), "cuda_graph": True}
+    ms = e0.elapsed_time(e1)
+    del graph, plan, plan_keep
+    job_ms, job_rate = ms, plan_pairs / (ms / 1000.0)
+    if world > 1:
+        # the job ends with its slowest rank; the pairs are every rank's
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(plan_pairs)], dtype=torch.float64, device="cuda")
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tp = t[1:].clone()
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+        job_ms, job_rate = float(tm.item()), float(tp.item()) / (float(tm.item()) / 1000.0)
+        return {"surfaces": count, "ranks": world, "scaling": "strong (the 64 surfaces split over the ranks)",
+                "shard_load": [float(v) for v in load], "pairs_per_s": job_rate, "ms": job_ms,
+                "cuda_graph": True}
+    # the same surfaces, one single-surface plan each (made, warmed by its autotuner, timed, freed), one
+    # after the other; the sum of their run times
+    ms_seq = 0.0
+    for sf, k in zip(surfs, ks):
+        sp = bie.Batch(ctx, [sf], [k], bie.KERNEL_S, W, slot)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sp.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+        del sp
+    mts = [sp["Mt"] for sp in specs]
+    return {"surfaces": count, "pairs": plan_pairs, "pairs_per_s": job_rate, "ms": job_ms,
+            "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms, "autotuned": plan_config,
+            "m_theta_counts": {str(m): mts.count(m) for m in sorted(set(mts))},
+            "panels_range": [min(sp["Np"] for sp in specs), max(sp["Np"] for sp in specs)],
+            "rhs_per_surface": [sp["nrhs"] for sp in specs],
+            "output": "ring of %d pairs x %d angles (throughput mode)" % (slot, maxMt), "cuda_graph": True,
+            "not_measured": "GGQ fill of the weights and the per-surface right-hand sides"}
 
 
 def learned_family(seed, i):
@@ -680,7 +728,7 @@ def main():
     ap.add_argument("--skip-solve", action="store_true")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned-preconditioner training and held-out solves")
-    ap.add_argument("--batch-surfaces", type=int, default=8, help="surfaces in the batch-scheduler run (0: skip)")
+    ap.add_argument("--batch-surfaces", type=int, default=64, help="surfaces in the batch-scheduler run (0: skip)")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: run the pair pipeline once on this many pairs of the workload and exit")
     args = ap.parse_args()

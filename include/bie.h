@@ -204,15 +204,22 @@ bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels
 #define BIE_UNWEIGHTED 0x100
 
 /* ---- batch scheduler -------------------------------------------------------
- * Many surfaces of uneven size (panels, Mth, wavenumber) in one persistent
- * launch.  bie_batch_create builds a device-resident plan: the near pairs of
- * every surface (all 16*Np*48*Mth enumerated (node, delta, g, theta) pairs,
- * invalid edge pairs give zero weights) are cut into items, ordered by
- * decreasing Mth, and an autotuner times item sizes {256, 1024, 4096} and CTA
- * shapes {1, 2, 4 warps} on a prefix of the list and keeps the fastest.
- * bie_batch_run resets the work counter and launches once: resident warps
- * claim items from the counter until the list is exhausted.  It allocates
- * nothing and can be captured in a CUDA graph (call it once before capture).
+ * Many surfaces of uneven size (panels, Mth, wavenumber) in a few launches.
+ * bie_batch_create builds a device-resident plan: the near pairs of every
+ * surface (all 16*Np*48*Mth enumerated (node, delta, g, theta) pairs, invalid
+ * edge pairs give zero weights) are cut into items and grouped by grid size
+ * Mth into classes, largest first, so that each class runs at the shared-
+ * memory carve and occupancy of its own Mth.
+ *  - Single layer alone (kernels = BIE_KERNEL_S): each class runs in chunks
+ *    through the root and transform kernels of bie_kernel_modes (per-pair
+ *    records in a plan-owned buffer of up to 2^20 pairs at the largest Mth);
+ *    the autotuner times chunks of 2^18, 2^19 and 2^20 pairs.
+ *  - With a double layer (K or KP): one persistent launch of the fused kernel
+ *    per class, resident warps claiming the class's items from an atomic
+ *    counter; the autotuner times item sizes {256, 1024, 4096} on a prefix.
+ * bie_batch_run resets the counters and launches the classes in order
+ * (bie_batch_launches kernels).  It allocates nothing and can be captured in a
+ * CUDA graph (call it once before capture).  At most 64 distinct Mth per plan.
  * Output: the Parseval weights of pair p of surface i (its enumerated index)
  * go to row (bie_batch_offset(plan, i) + p) % slot_pairs of weights_out [dev]
  * double2[nk][slot_pairs][max Mth] (row length = largest Mth of the batch;
@@ -226,6 +233,15 @@ bie_status bie_batch_run(bie_batch plan);
 int64_t bie_batch_pairs(bie_batch plan);
 int64_t bie_batch_offset(bie_batch plan, int i);
 void bie_batch_config(bie_batch plan, int* item_pairs, int* warps_per_block, int* blocks);
+int bie_batch_launches(bie_batch plan);
+
+/* bie_shard_surfaces: split n independent surfaces over world ranks (one GPU
+ * each) for batches that do not fit one GPU.  Surfaces share no pairs, so each
+ * rank makes a plan of its own surfaces and no data moves between ranks.
+ * Greedy longest-processing-time order: owner[i] in [0, world) for cost[i] >= 0
+ * (e.g. near pairs times log Mth), load[r] (may be NULL) the summed cost of rank
+ * r.  Host only: no device call.  Errors: BIE_EINVAL.                         */
+bie_status bie_shard_surfaces(int n, const double* cost, int world, int* owner, double* load);
 void bie_batch_free(bie_batch plan);
 
 /* ---- assembly (Section 3.4, Eq. (S1), Section 4) --------------------------

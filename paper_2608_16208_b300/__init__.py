@@ -434,10 +434,24 @@ _sig("bie_batch_pairs", _i64, [_vp])
 _sig("bie_batch_offset", _i64, [_vp, _i32])
 _sig("bie_batch_config", None, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)])
 _sig("bie_batch_free", None, [_vp])
+_sig("bie_batch_launches", _i32, [_vp])
+_sig("bie_shard_surfaces", _i32, [_i32, _vp, _i32, _vp, _vp])
+
+
+def shard_surfaces(costs, world):
+    """Owner rank of each surface (greedy longest-processing-time over world ranks) and the ranks' loads."""
+    c = np.ascontiguousarray(np.asarray(costs, dtype=np.float64))
+    owner = np.empty(len(c), dtype=np.int32)
+    load = np.empty(world, dtype=np.float64)
+    check(lib.bie_shard_surfaces(len(c), c.ctypes.data_as(_vp), int(world), owner.ctypes.data_as(_vp),
+                                 load.ctypes.data_as(_vp)), "bie_shard_surfaces")
+    return owner, load
 
 
 class Batch:
-    """A device-resident plan running the pair pipeline of many surfaces in one persistent launch."""
+    """A device-resident plan running the pair pipeline of many surfaces in a few launches (one class of
+    equal grid size after another: chunks through the root and transform kernels for the single layer,
+    one persistent launch per class with a double layer)."""
 
     def __init__(self, ctx, surfaces, ks, kernels, weights, slot_pairs):
         self.ctx, self.surfaces, self.weights = ctx, list(surfaces), weights
@@ -450,7 +464,8 @@ class Batch:
         self.offsets = [lib.bie_batch_offset(self.h, i) for i in range(len(surfaces))]
         a, b, c = _i32(), _i32(), _i32()
         lib.bie_batch_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
-        self.config = {"item_pairs": a.value, "warps_per_block": b.value, "blocks": c.value}
+        self.config = {"item_pairs": a.value, "warps_per_block": b.value, "blocks": c.value,
+                       "launches": lib.bie_batch_launches(self.h)}
 
     def run(self):
         check(lib.bie_batch_run(self.h), "bie_batch_run")

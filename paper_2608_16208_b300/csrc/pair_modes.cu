@@ -1498,9 +1498,15 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
 }
 
 // ------------------------------------------------------------------ batch scheduler
-// Many surfaces of uneven size (panels, Mth, k) in one persistent launch: the near pairs of every
-// surface are cut into items of a fixed number of pairs, ordered by decreasing Mth (longest work
-// first), and resident warps claim items from an atomic counter until the list is exhausted.
+// Many surfaces of uneven size (panels, Mth, k) in a few launches.  The near pairs of every surface
+// are cut into items of item_pairs pairs and grouped by grid size Mth into classes, largest first.
+//  * Single layer alone: each class runs in chunks through the two kernels of the single-surface path
+//    (the root kernel, then the transform kernel over per-pair records), each at the shared-memory
+//    carve and occupancy of the class's own Mth; warps take the chunk's 32-pair batches in a fixed
+//    order (the work of a batch hardly varies within a class).
+//  * With a double layer: one persistent launch of the fused kernel per class, resident warps
+//    claiming the class's items from an atomic counter (longest work first across classes).
+// Nothing is allocated by a run, so a run can be captured in a CUDA graph.
 namespace bie {
 struct BatchItem {
   int surf;
@@ -1508,21 +1514,30 @@ struct BatchItem {
   int64_t p0;   // first enumerated pair of the item within its surface
 };
 
+// per-pair records of one chunk of a class (split path)
+struct BatchRec {
+  double* hdr;
+  float4* E;
+  double* A;
+  double* R2;
+  int Mt, L;
+};
+
 template <bool kWithK>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
-    pair_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int n_items,
-                      int* __restrict__ counter, double* __restrict__ scratch, int64_t scratch_per_warp, int maxMt) {
+    pair_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int it0, int it1,
+                      int* __restrict__ counter, double* __restrict__ scratch, int64_t scratch_per_warp, int Mt) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const size_t per_warp = smem_doubles(maxMt, (kWithK ? 4 : 3) * maxMt, (kWithK ? 4 : 3) * (maxMt / 2), kWithK);
+  const size_t per_warp = smem_doubles(Mt, (kWithK ? 4 : 3) * Mt, (kWithK ? 4 : 3) * (Mt / 2), kWithK);
   double* wbase = smem + per_warp * wib;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   double* scrA = scratch + gwarp * scratch_per_warp;
-  for (int guard = 0; guard <= n_items; ++guard) {   // each pass claims one item; bounded by the list length
+  for (int guard = 0; guard <= it1 - it0; ++guard) {   // each pass claims one item; bounded by the list length
     int it = 0;
-    if (lane == 0) it = atomicAdd(counter, 1);
+    if (lane == 0) it = it0 + atomicAdd(counter, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n_items) break;
+    if (it >= it1) break;
     const BatchItem item = items[it];
     const PairArgs& a = surfs[item.surf];
     const Smem sm = carve(wbase, a.Mt, a.P, a.L, kWithK);
@@ -1530,25 +1545,106 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
     for (int q = 0; q < item.n; q += 32) process_batch<kWithK>(a, sm, scrA, scrD, item.p0 + q, min(32, item.n - q));
   }
 }
+
+// 32-pair batch wb of a chunk of items [it0, it0 + nit): item it0 + wb / (item_pairs / 32), offset
+// (wb mod (item_pairs / 32)) * 32 in it; its records start at slot 32 wb of the chunk.
+__global__ void __launch_bounds__(128)
+    pair_root_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int it0, int nit,
+                           int item_pairs, const BatchRec rec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int wpi = item_pairs / 32;
+  for (int64_t wb = gwarp; wb < (int64_t)nit * wpi; wb += nwarps) {
+    const BatchItem item = items[it0 + wb / wpi];
+    const int off = (int)(wb % wpi) * 32;
+    if (off >= item.n) continue;
+    const PairArgs& a = surfs[item.surf];
+    const int nb = min(32, item.n - off);
+    const int64_t r0 = wb * 32;
+    PairInfo mine;
+    unsigned vm;
+    front_batch<false>(a, Smem{}, item.p0 + off, nb, rec.R2 + r0 * rec.Mt, rec.E + r0 * 33, rec.A + r0 * (rec.L + 1),
+                       rec.L + 1, 1, nullptr, mine, vm);
+    if (lane < nb) {
+      double* h = rec.hdr + (r0 + lane) * 8;
+      h[0] = mine.a;
+      h[1] = mine.qb;
+      h[2] = mine.om;
+      h[3] = mine.sha;
+      h[4] = mine.cha;
+      h[5] = mine.valid ? 1.0 : 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
+    pair_transform_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int it0,
+                                int nit, int item_pairs, const BatchRec rec) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int Mt = rec.Mt, L = rec.L;
+  const size_t per_warp = smem_doubles(Mt, 3 * Mt, L, false);
+  const Smem sm = carve(smem + per_warp * wib, Mt, 3 * Mt, L, false);
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int wpi = item_pairs / 32;
+  for (int64_t wb = gwarp; wb < (int64_t)nit * wpi; wb += nwarps) {
+    const BatchItem item = items[it0 + wb / wpi];
+    const int off = (int)(wb % wpi) * 32;
+    if (off >= item.n) continue;
+    const PairArgs& a = surfs[item.surf];
+    const int nb = min(32, item.n - off);
+    const int64_t r0 = wb * 32;
+    PairInfo mine = {};
+    if (lane < nb) {
+      const double* h = rec.hdr + (r0 + lane) * 8;
+      mine.a = h[0];
+      mine.qb = h[1];
+      mine.om = h[2];
+      mine.sha = h[3];
+      mine.cha = h[4];
+      mine.valid = h[5] != 0.0;
+    }
+    const unsigned vm = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
+    phase_d_single(a, sm, reinterpret_cast<const float2*>(rec.A + r0 * (L + 1)), L + 1, 1, rec.E + r0 * 33,
+                   rec.R2 + r0 * Mt, mine, vm, item.p0 + off, nb);
+  }
+}
+
+constexpr int kMaxBatchClasses = 64;   // distinct grid sizes in one plan
+
+struct BatchClass {
+  int Mt;
+  int it_begin, it_end;   // item range of the class (items sorted by decreasing Mth)
+  // fused path
+  int wpb = 0, blocks = 0;
+  size_t smem = 0;
+  // split path
+  int root_blocks = 0, tr_wpb = 0, tr_blocks = 0;
+  size_t tr_smem = 0;
+};
 }  // namespace bie
 
 struct bie_batch_s {
   bie_ctx ctx;
   unsigned kernels;
-  bool withK;
-  int n_surf, maxMt, wpb, item_pairs, blocks, n_items;
-  size_t smem;
+  bool withK, split;
+  int n_surf, maxMt, item_pairs, n_items, chunk_items;
   int64_t total_pairs, scratch_per_warp;
   std::vector<bie::PairArgs> host_args;
   std::vector<int64_t> offsets;
-  bie::PairArgs* d_args;
-  bie::BatchItem* d_items;
-  int* d_counter;
-  double* scratch;
-  float tuned_ms;
+  std::vector<bie::BatchClass> classes;
+  bie::PairArgs* d_args = nullptr;
+  bie::BatchItem* d_items = nullptr;
+  int* d_counter = nullptr;     // one counter per class (fused path)
+  double* scratch = nullptr;    // fused path: per resident warp recurrence scratch
+  double* records = nullptr;    // split path: per-pair records of one chunk
+  float tuned_ms = 0.f;
 };
 
 namespace bie {
+// items of every surface, ordered by decreasing Mth (stable: surfaces keep their order within a class)
 static std::vector<BatchItem> make_items(const bie_batch_s& b, int item_pairs) {
   std::vector<BatchItem> items;
   for (int sidx = 0; sidx < b.n_surf; ++sidx) {
@@ -1562,49 +1658,130 @@ static std::vector<BatchItem> make_items(const bie_batch_s& b, int item_pairs) {
   return items;
 }
 
-// The dynamic shared-memory limit is a property of the kernel function, shared by every plan:
-// it only grows, so a plan configured earlier (or captured in a graph) keeps launching.
-static int g_batch_smem_attr[2] = {0, 0};
-static bie_status batch_smem_attr(bool withK, size_t smem) {
-  int& cur = g_batch_smem_attr[withK ? 1 : 0];
+static std::vector<BatchClass> make_classes(const bie_batch_s& b, const std::vector<BatchItem>& items) {
+  std::vector<BatchClass> cl;
+  for (int i = 0; i < (int)items.size(); ++i) {
+    const int Mt = b.host_args[items[i].surf].Mt;
+    if (cl.empty() || cl.back().Mt != Mt) {
+      BatchClass c;
+      c.Mt = Mt;
+      c.it_begin = i;
+      cl.push_back(c);
+    }
+    cl.back().it_end = i + 1;
+  }
+  return cl;
+}
+
+// Dynamic shared-memory limits are properties of the kernel functions, shared by every plan: they
+// only grow (set when a plan is made, never during a run), so earlier plans and captured graphs keep
+// launching.
+static int g_batch_smem_attr[3] = {0, 0, 0};
+static bie_status grow_smem_attr(int which, size_t smem) {
+  int& cur = g_batch_smem_attr[which];
   if ((int)smem <= cur) return BIE_OK;
-  auto kern = withK ? pair_batch_kernel<true> : pair_batch_kernel<false>;
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_batch_kernel)");
+  const void* f = which == 0 ? (const void*)pair_batch_kernel<false>
+                  : which == 1 ? (const void*)pair_batch_kernel<true>
+                               : (const void*)pair_transform_batch_kernel;
+  const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch kernel)");
   cur = (int)smem;
   return BIE_OK;
 }
 
-static bie_status batch_launch(bie_batch_s& b, int n_items) {
-  cudaStream_t st = b.ctx->stream;
-  const bie_status as = batch_smem_attr(b.withK, b.smem);
-  if (as != BIE_OK) return as;
-  cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
-  if (b.withK)
-    pair_batch_kernel<true><<<b.blocks, 32 * b.wpb, b.smem, st>>>(b.d_args, b.d_items, n_items, b.d_counter, b.scratch,
-                                                                   b.scratch_per_warp, b.maxMt);
-  else
-    pair_batch_kernel<false><<<b.blocks, 32 * b.wpb, b.smem, st>>>(b.d_args, b.d_items, n_items, b.d_counter, b.scratch,
-                                                                    b.scratch_per_warp, b.maxMt);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "pair_batch_kernel");
+static int64_t split_record_doubles(int Mt) {
+  const int L = 3 * (Mt / 2);
+  return 8 + 2 * 33 + (L + 1) + Mt;
 }
 
-// configure grid, shared memory and scratch for a CTA shape; returns false if it does not fit
-static bool batch_configure(bie_batch_s& b, int wpb) {
-  const int P = (b.withK ? 4 : 3) * b.maxMt, L = (b.withK ? 4 : 3) * (b.maxMt / 2);
-  const size_t per = smem_doubles(b.maxMt, P, L, b.withK) * sizeof(double);
-  if (per * wpb > kSmemLimit) return false;
-  auto kern = b.withK ? pair_batch_kernel<true> : pair_batch_kernel<false>;
-  if (batch_smem_attr(b.withK, per * wpb) != BIE_OK) return false;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, per * wpb) != cudaSuccess || per_sm < 1)
-    return false;
-  b.wpb = wpb;
-  b.smem = per * wpb;
-  b.blocks = b.ctx->sms * per_sm;
-  return true;
+static BatchRec class_records(const bie_batch_s& b, const BatchClass& c) {
+  const int64_t slots = (int64_t)b.chunk_items * b.item_pairs;
+  BatchRec r;
+  r.Mt = c.Mt;
+  r.L = 3 * (c.Mt / 2);
+  r.hdr = b.records;
+  r.E = reinterpret_cast<float4*>(b.records + 8 * slots);
+  r.A = b.records + (8 + 2 * 33) * slots;
+  r.R2 = r.A + (int64_t)(r.L + 1) * slots;
+  return r;
+}
+
+// configure one class: CTA shapes and grids for its kernels; false if it does not fit
+static bool configure_class(bie_batch_s& b, BatchClass& c) {
+  const int sms = b.ctx->sms;
+  if (!b.split) {
+    const bool wk = b.withK;
+    const int P = (wk ? 4 : 3) * c.Mt, L = (wk ? 4 : 3) * (c.Mt / 2);
+    const size_t per = smem_doubles(c.Mt, P, L, wk) * sizeof(double);
+    auto kern = wk ? pair_batch_kernel<true> : pair_batch_kernel<false>;
+    int best = 0;
+    for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
+      if (per * w > kSmemLimit || grow_smem_attr(wk ? 1 : 0, per * w) != BIE_OK) continue;
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * w, per * w) != cudaSuccess) continue;
+      if (nb * w > best) { best = nb * w; c.wpb = w; c.smem = per * w; c.blocks = sms * nb; }
+    }
+    return best > 0;
+  }
+  int per_r = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, pair_root_batch_kernel, 128, 0) != cudaSuccess) return false;
+  c.root_blocks = sms * std::max(per_r, 1);
+  const size_t per = smem_doubles(c.Mt, 3 * c.Mt, 3 * (c.Mt / 2), false) * sizeof(double);
+  int best = 0;
+  for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
+    if (per * w > kSmemLimit || grow_smem_attr(2, per * w) != BIE_OK) continue;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_transform_batch_kernel, 32 * w, per * w) != cudaSuccess)
+      continue;
+    if (nb * w > best) { best = nb * w; c.tr_wpb = w; c.tr_smem = per * w; c.tr_blocks = sms * nb; }
+  }
+  return best > 0;
+}
+
+// launch every class; items at or past it_hi are left out (the autotuner times a prefix)
+static bie_status batch_launch(bie_batch_s& b, int it_hi) {
+  cudaStream_t st = b.ctx->stream;
+  if (!b.split) {
+    cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int) * b.classes.size(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
+    for (size_t ci = 0; ci < b.classes.size(); ++ci) {
+      const BatchClass& c = b.classes[ci];
+      const int end = std::min(c.it_end, it_hi);
+      if (end <= c.it_begin) break;
+      if (b.withK)
+        pair_batch_kernel<true><<<c.blocks, 32 * c.wpb, c.smem, st>>>(b.d_args, b.d_items, c.it_begin, end,
+                                                                      b.d_counter + ci, b.scratch, b.scratch_per_warp, c.Mt);
+      else
+        pair_batch_kernel<false><<<c.blocks, 32 * c.wpb, c.smem, st>>>(b.d_args, b.d_items, c.it_begin, end,
+                                                                       b.d_counter + ci, b.scratch, b.scratch_per_warp, c.Mt);
+    }
+  } else {
+    for (const BatchClass& c : b.classes) {
+      const int end = std::min(c.it_end, it_hi);
+      if (end <= c.it_begin) break;
+      const BatchRec rec = class_records(b, c);
+      for (int i0 = c.it_begin; i0 < end; i0 += b.chunk_items) {
+        const int nit = std::min(b.chunk_items, end - i0);
+        const int64_t wbs = (int64_t)nit * (b.item_pairs / 32);
+        const int br = (int)std::max<int64_t>(1, std::min<int64_t>(c.root_blocks, (wbs + 3) / 4));
+        pair_root_batch_kernel<<<br, 128, 0, st>>>(b.d_args, b.d_items, i0, nit, b.item_pairs, rec);
+        const int bt = (int)std::max<int64_t>(1, std::min<int64_t>(c.tr_blocks, (wbs + c.tr_wpb - 1) / c.tr_wpb));
+        pair_transform_batch_kernel<<<bt, 32 * c.tr_wpb, c.tr_smem, st>>>(b.d_args, b.d_items, i0, nit, b.item_pairs,
+                                                                         rec);
+      }
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "batch kernels");
+}
+
+static bie_status upload_items(bie_batch_s& b, const std::vector<BatchItem>& items) {
+  if (b.d_items) cudaFree(b.d_items);
+  b.d_items = nullptr;
+  cudaError_t e = cudaMalloc((void**)&b.d_items, sizeof(BatchItem) * items.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b.d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "batch items");
 }
 }  // namespace bie
 
@@ -1623,13 +1800,20 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
   b->ctx = ctx;
   b->kernels = kernels;
   b->withK = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
+  b->split = !b->withK;
   b->n_surf = n_surf;
   b->maxMt = 0;
+  std::vector<int> grids;
   for (int i = 0; i < n_surf; ++i) {
     if (!surfs[i] || !(ks[i] > 0) || !(ks[i] < 1e6)) { delete b; set_error("bie_batch_create: surface %d or k invalid", i); return BIE_EINVAL; }
     b->maxMt = surfs[i]->Mt > b->maxMt ? surfs[i]->Mt : b->maxMt;
+    if (std::find(grids.begin(), grids.end(), surfs[i]->Mt) == grids.end()) grids.push_back(surfs[i]->Mt);
   }
-  const int nk = (kernels & BIE_KERNEL_S ? 1 : 0) + (b->withK ? 1 : 0);
+  if (grids.size() > (size_t)kMaxBatchClasses) {
+    delete b;
+    set_error("bie_batch_create: more than %d grid sizes", kMaxBatchClasses);
+    return BIE_EUNSUPPORTED;
+  }
   int64_t off = 0;
   for (int i = 0; i < n_surf; ++i) {
     PairArgs a = make_pair_args(surfs[i], ks[i], kernels);
@@ -1645,7 +1829,6 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     off += a.n_pairs;
     b->host_args.push_back(a);
   }
-  (void)nk;
   b->total_pairs = off;
   const double* rec = nullptr;
   int rec_len = 0;
@@ -1656,57 +1839,82 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     a.rec_len = rec_len;
   }
   cudaError_t e = cudaMalloc((void**)&b->d_args, sizeof(PairArgs) * n_surf);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
-  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch)"); }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int) * kMaxBatchClasses);
+  if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "cudaMalloc(batch)"); }
   e = cudaMemcpy(b->d_args, b->host_args.data(), sizeof(PairArgs) * n_surf, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "cudaMemcpy(batch args)"); }
-  b->scratch_per_warp = pair_scratch_per_warp((b->withK ? 4 : 3) * (b->maxMt / 2), b->withK, b->maxMt);
-  // ---- autotuner: item size x CTA shape, timed on a prefix of the work list (about 1/16 of the pairs)
-  const int item_cands[3] = {256, 1024, 4096};
-  const int wpb_cands[3] = {1, 2, 4};
-  float best = 1e30f;
-  int best_item = 1024, best_wpb = 0;
-  b->d_items = nullptr;
-  b->scratch = nullptr;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  size_t max_scratch = 0;
-  for (int wi = 0; wi < 3; ++wi) {
-    if (!batch_configure(*b, wpb_cands[wi])) continue;
-    max_scratch = std::max(max_scratch, sizeof(double) * (size_t)b->scratch_per_warp * b->blocks * b->wpb);
-  }
-  e = cudaMalloc((void**)&b->scratch, max_scratch);
-  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return cuda_fail(e, "cudaMalloc(batch scratch)"); }
-  for (int ii = 0; ii < 3; ++ii) {
-    std::vector<BatchItem> items = make_items(*b, item_cands[ii]);
-    if (b->d_items) cudaFree(b->d_items);
-    e = cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items.size());
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return cuda_fail(e, "batch items"); }
-    const int prefix = (int)std::max<size_t>(1, items.size() / 16);
-    for (int wi = 0; wi < 3; ++wi) {
-      if (!batch_configure(*b, wpb_cands[wi])) continue;
-      cudaEventRecord(e0, ctx->stream);
-      st = batch_launch(*b, prefix);
-      cudaEventRecord(e1, ctx->stream);
-      if (st != BIE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); bie_batch_free(b); return st; }
-      cudaEventSynchronize(e1);
+  auto timed = [&](int it_hi, float* ms) -> bie_status {
+    cudaEventRecord(e0, ctx->stream);
+    const bie_status s2 = batch_launch(*b, it_hi);
+    cudaEventRecord(e1, ctx->stream);
+    if (s2 != BIE_OK) return s2;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return BIE_OK;
+  };
+  float best = 1e30f;
+  if (b->split) {
+    // items of 1024 pairs; the autotuner picks the chunk (records of 2^18, 2^19 or 2^20 pairs) on the
+    // first 2^20 pairs of the largest class
+    b->item_pairs = 1024;
+    const std::vector<BatchItem> items = make_items(*b, b->item_pairs);
+    b->n_items = (int)items.size();
+    b->classes = make_classes(*b, items);
+    st = upload_items(*b, items);
+    for (auto& c : b->classes)
+      if (st == BIE_OK && !configure_class(*b, c)) { st = BIE_EUNSUPPORTED; set_error("bie_batch_create: a class does not fit"); }
+    const int cands[3] = {256, 512, 1024};
+    size_t rbytes = sizeof(double) * (size_t)split_record_doubles(b->maxMt) * 1024 * 1024;
+    if (st == BIE_OK && (e = cudaMalloc((void**)&b->records, rbytes)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc(batch records)");
+    int best_c = 1024;
+    const int probe = std::min(b->classes[0].it_end, 1024);
+    for (int ci = 0; ci < 3 && st == BIE_OK; ++ci) {
+      b->chunk_items = cands[ci];
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_item = item_cands[ii]; best_wpb = wpb_cands[wi]; }
+      st = timed(probe, &ms);
+      if (st == BIE_OK && ms < best) { best = ms; best_c = cands[ci]; }
+    }
+    b->chunk_items = best_c;
+  } else {
+    // the fused kernel: the autotuner picks the item size on a prefix of the work list; each class
+    // runs at the CTA shape with the most resident warps for its Mth
+    const int cands[3] = {256, 1024, 4096};
+    int best_item = 1024;
+    b->scratch_per_warp = pair_scratch_per_warp((b->withK ? 4 : 3) * (b->maxMt / 2), b->withK, b->maxMt);
+    size_t max_warps = 0;
+    for (int ii = 0; ii < 3 && st == BIE_OK; ++ii) {
+      b->item_pairs = cands[ii];
+      const std::vector<BatchItem> items = make_items(*b, b->item_pairs);
+      b->classes = make_classes(*b, items);
+      for (auto& c : b->classes)
+        if (!configure_class(*b, c)) { st = BIE_EUNSUPPORTED; set_error("bie_batch_create: a class does not fit"); }
+      for (auto& c : b->classes) max_warps = std::max(max_warps, (size_t)c.blocks * c.wpb);
+      if (st != BIE_OK) break;
+      if (!b->scratch) {
+        e = cudaMalloc((void**)&b->scratch, sizeof(double) * (size_t)b->scratch_per_warp * max_warps);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMalloc(batch scratch)"); break; }
+      }
+      st = upload_items(*b, items);
+      if (st != BIE_OK) break;
+      float ms = 0.f;
+      st = timed(std::max<int>(1, (int)items.size() / 16), &ms);
+      if (st == BIE_OK && ms < best) { best = ms; best_item = cands[ii]; }
+    }
+    if (st == BIE_OK) {
+      b->item_pairs = best_item;
+      const std::vector<BatchItem> items = make_items(*b, b->item_pairs);
+      b->n_items = (int)items.size();
+      b->classes = make_classes(*b, items);
+      for (auto& c : b->classes) configure_class(*b, c);
+      st = upload_items(*b, items);
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!best_wpb || !batch_configure(*b, best_wpb)) { bie_batch_free(b); set_error("bie_batch_create: no CTA shape fits"); return BIE_EUNSUPPORTED; }
-  std::vector<BatchItem> items = make_items(*b, best_item);
-  cudaFree(b->d_items);
-  e = cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items.size());
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) { bie_batch_free(b); return cuda_fail(e, "batch items"); }
-  b->n_items = (int)items.size();
-  b->item_pairs = best_item;
+  if (st != BIE_OK) { bie_batch_free(b); return st; }
   b->tuned_ms = best;
   *out = b;
   return BIE_OK;
@@ -1725,9 +1933,18 @@ extern "C" int64_t bie_batch_offset(bie_batch b, int i) {
 
 extern "C" void bie_batch_config(bie_batch b, int* item_pairs, int* warps_per_block, int* blocks) {
   if (!b) return;
-  if (item_pairs) *item_pairs = b->item_pairs;
-  if (warps_per_block) *warps_per_block = b->wpb;
-  if (blocks) *blocks = b->blocks;
+  if (item_pairs) *item_pairs = b->split ? b->chunk_items * b->item_pairs : b->item_pairs;
+  const BatchClass* c = b->classes.empty() ? nullptr : &b->classes[0];
+  if (warps_per_block) *warps_per_block = c ? (b->split ? c->tr_wpb : c->wpb) : 0;
+  if (blocks) *blocks = c ? (b->split ? c->tr_blocks : c->blocks) : 0;
+}
+
+extern "C" int bie_batch_launches(bie_batch b) {
+  if (!b) return 0;
+  if (!b->split) return (int)b->classes.size();
+  int n = 0;
+  for (const BatchClass& c : b->classes) n += 2 * ((c.it_end - c.it_begin + b->chunk_items - 1) / b->chunk_items);
+  return n;
 }
 
 extern "C" void bie_batch_free(bie_batch b) {
@@ -1736,5 +1953,6 @@ extern "C" void bie_batch_free(bie_batch b) {
   cudaFree(b->d_items);
   cudaFree(b->d_counter);
   cudaFree(b->scratch);
+  cudaFree(b->records);
   delete b;
 }

@@ -48,3 +48,48 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(Args())
     assert capsys.readouterr().out == ""
+
+
+def _shard_rank(rank, world, port, out):
+    """One rank of the sharded batch: the library's assignment, then the job figures by all_reduce."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    import paper_2608_16208_b300 as bie
+    import workloads as wl
+    import numpy as np
+    specs = wl.batch_surfaces(seed=0, count=64)
+    costs = [16 * sp["Np"] * 48 * sp["Mt"] * np.log2(sp["Mt"]) for sp in specs]
+    owner, load = bie.shard_surfaces(costs, world)
+    mine = [i for i in range(64) if owner[i] == rank]
+    # every rank computes the same assignment, so the shares partition the batch
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    t = torch.tensor([float(sum(costs[i] for i in mine))], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    out[rank] = (gathered, float(t.item()), [float(v) for v in load])
+    dist.destroy_process_group()
+
+
+def test_sharded_batch_partitions_the_surfaces():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_shard_rank, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
+        res = dict(out)
+    gathered, worst, load = res[0]
+    assert res[1][0] == gathered
+    every = sorted(i for share in gathered for i in share)
+    assert every == list(range(64))
+    assert abs(worst - max(load)) <= 1e-9 * worst
+    # longest-processing-time keeps the largest load within 4/3 of the balanced share
+    assert max(load) <= (4.0 / 3.0) * sum(load) / world
+
+
+def test_shard_assignment_is_greedy_lpt():
+    import paper_2608_16208_b300 as bie
+    owner, load = bie.shard_surfaces([5.0, 1.0, 4.0, 3.0, 3.0], 2)
+    # in decreasing cost 5, 4, 3, 3, 1 (equal costs keep their order), each to the least-loaded rank:
+    # 5 -> 0, 4 -> 1, 3 -> 1 (4 < 5), 3 -> 0 (5 < 7), 1 -> 1 (7 < 8)
+    assert list(owner) == [0, 1, 1, 1, 0]
+    assert list(load) == [8.0, 8.0]
