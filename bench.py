@@ -719,6 +719,56 @@ def run_kernel_only(n):
     print("kernel-only: %d pairs, finite: %s" % (n, bool(torch.isfinite(torch.view_as_real(out)).all())))
 
 
+def run_profile_case(name):
+    """Profiling aid: one small launch of a kernel family, sized for an ncu capture (inputs above the
+    126 MB L2, a few GB on the device at most).  Prints what ran."""
+    import torch
+    import paper_2608_16208_b300 as bie
+    ggq = wl.load_ggq()
+    ctx = bie.Context()
+    c = wl.config(WORKLOAD)
+    if name == "assemble":        # far fill and near fill of S on Np = 4, Mth = 128 (N = 8,192; 1.07 GB)
+        s = bie.Surface(ctx, c["surface"], 4, c["Mt"], ggq)
+        A = bie.assemble(s, bie.OP_S, c["k"])
+        ctx.sync()
+        print("assemble: N = %d" % s.N)
+    elif name == "products":      # block products, 5 right-hand sides, N = 8,192 (FP64 1.07 GB)
+        s = bie.Surface(ctx, c["surface"], 4, c["Mt"], ggq)
+        A = bie.assemble(s, bie.OP_CFIE | bie.UNWEIGHTED, c["k"])
+        M = bie.Matrix(ctx, A, bie.STORE_FP32 | bie.STORE_BF16X2)
+        X = torch.as_tensor(wl.random_complex((5, s.N), 3, 7), dtype=torch.complex128).cuda()
+        for prec in (0, 1, 2, 3):
+            M.matvec(X, prec)
+        ctx.sync()
+        print("products: N = %d, 5 right-hand sides, precisions 0-3" % s.N)
+    elif name == "field":         # field evaluation, 32,768 sources x 1,024 points
+        s = bie.Surface(ctx, c["surface"], c["Np"], c["Mt"], ggq)
+        dens = torch.as_tensor(wl.random_complex((s.N,), 0, 13), dtype=torch.complex128).cuda()
+        bie.field_eval(s, bie.OP_S, c["k"], dens, wl.exterior_points(1024, 3.0))
+        ctx.sync()
+        print("field: %d sources x 1024 points" % s.N)
+    elif name == "batch":         # the split batch path: four harmonic stars, Mth 64..256
+        specs = wl.batch_surfaces(seed=0, count=4)
+        surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
+        W = torch.empty((1, 1 << 18, max(sp["Mt"] for sp in specs)), dtype=torch.complex128, device="cuda")
+        plan = bie.Batch(ctx, surfs, [sp["k"] for sp in specs], bie.KERNEL_S, W, 1 << 18)
+        plan.run()
+        ctx.sync()
+        print("batch: %d pairs, config %s" % (plan.pairs, plan.config))
+    elif name == "precond":       # block-diagonal factors and one training step of the network, N = 24,576
+        desc, k, d = learned_family(1, 0)
+        s = bie.Surface(ctx, desc, 16, 96, ggq)
+        A = bie.assemble(s, bie.OP_S, k)
+        B = bie.BlockDiag(ctx, A, 16 * 96)
+        ts = bie.TrainSet(ctx, s, k, A, B)
+        net = bie.Net(ctx, seed=1)
+        net.train([ts], steps=2, batch=16, lr=1e-3, seed=2)
+        ctx.sync()
+        print("precond: N = %d" % s.N)
+    else:
+        raise SystemExit("unknown profile case %r" % name)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -729,10 +779,15 @@ def main():
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned-preconditioner training and held-out solves")
     ap.add_argument("--batch-surfaces", type=int, default=64, help="surfaces in the batch-scheduler run (0: skip)")
+    ap.add_argument("--profile-case", default="",
+                    help="profiling aid: one small launch of a kernel family (assemble, products, field, batch, "
+                         "precond) and exit")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: run the pair pipeline once on this many pairs of the workload and exit")
     args = ap.parse_args()
-    if args.kernel_only:
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+    elif args.kernel_only:
         run_kernel_only(args.kernel_only)
     elif args.impl == "reference":
         run_reference(args)

@@ -167,6 +167,16 @@ __device__ inline void ellipke(double m, double m1, double* K, double* E) {
   *E = *K * (1.0 - c2sum);
 }
 
+// Exponent e (|e| <= 60) with 2^e close to rms(x) / rms(y), from the warp-summed squares sx, sy; 0 when
+// either part is zero.  Two real signals packed in one complex transform each come out with an error
+// in proportion to the larger of the two: the smaller is multiplied by this exact power of two before
+// packing and divided by it after.
+__device__ __forceinline__ int pack_exponent(double sx, double sy) {
+  if (!(sx > 0.0) || !(sy > 0.0)) return 0;
+  const int e = (int)rint(0.5 * log2(sx / sy));
+  return max(-60, min(60, e));
+}
+
 // ------------------------------------------------------------------ phase B: root (one lane)
 struct PairInfo {
   int64_t row, ring;
@@ -821,22 +831,28 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       auto Am = [&](int m) { return scrA[m * 32 + pi]; };
       auto Bm = [&](int m) { return -(m - 0.5) * fac * (scrD[m * 32 + pi] + 2 * sh2b * scrA[m * 32 + pi]); };
       // ---- D2. circulant transforms: A_{|d|} (|d| <= P/2) and B_{|d|} or B~_{|d|} (|d| <= 2M)
-      for (int pp = lane; pp < P; pp += 32) {
-        const int dd = pp <= P / 2 ? pp : P - pp;
-        const double av = dd <= L ? Am(dd) : 0.0;
-        double bv = 0.0;
-        if (dd <= 2 * M) {
-          bv = Bm(dd);
-          if (translated) bv = (Am(dd) - om * om * bv) / (4 * qb);
-        }
-        sm.W1[pp] = C(av, bv);
-      }
-      __syncwarp();
       {
+        double sa = 0.0, sb = 0.0;
+        for (int pp = lane; pp < P; pp += 32) {
+          const int dd = pp <= P / 2 ? pp : P - pp;
+          const double av = dd <= L ? Am(dd) : 0.0;
+          double bv = 0.0;
+          if (dd <= 2 * M) {
+            bv = Bm(dd);
+            if (translated) bv = (Am(dd) - om * om * bv) / (4 * qb);
+          }
+          sa += av * av;
+          sb += bv * bv;
+          sm.W1[pp] = C(av, bv);
+        }
+        const int eb = pack_exponent(warp_sum(sa), warp_sum(sb));   // B scaled to A's size for the packing
+        const double up = ldexp(1.0, eb), down = ldexp(1.0, -eb);
+        for (int pp = lane; pp < P; pp += 32) sm.W1[pp].im *= up;
+        __syncwarp();
         const cplx* Af = warp_fft(sm.W1, sm.W0, P, a.tw, a.T, -1);
         for (int pp = lane; pp < P; pp += 32) {
           sm.Acal[pp] = Af[pp].re;
-          sm.Bcal[pp] = Af[pp].im;
+          sm.Bcal[pp] = Af[pp].im * down;
         }
       }
       __syncwarp();
@@ -974,15 +990,27 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         emit(p, 0, true, sm.kc);
       }
       // ---- D5. A~ <- V_K A~ = alpha~ tau0~ F~ A~ on the P grid
-      for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], sm.alph[q]);
+      {
+        // tau_0 (~ kappa rho^2, amplified ~50x in K) packed with alpha (~k^2/2) scaled to tau_0's size
+        double st0 = 0.0, sal = 0.0;
+        for (int q = lane; q < Mt; q += 32) {
+          st0 += sm.tau0[q] * sm.tau0[q];
+          sal += sm.alph[q] * sm.alph[q];
+        }
+        const int ea = pack_exponent(warp_sum(st0), warp_sum(sal));
+        const double up = ldexp(1.0, ea), down = ldexp(1.0, -ea);
+        for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.tau0[q], sm.alph[q] * up);
+        __syncwarp();
+        cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
+        cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
+        cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.twf, a.T, false);   // re: tau0~, im: 2^ea alpha~
+        for (int pp = lane; pp < P; pp += 32) sm.Acal[pp] = up2[pp].re * (up2[pp].im * down) * sm.Acal[pp];
+      }
       __syncwarp();
-      cplx* Z2 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
-      cplx* Zf2 = (Z2 == sm.W0) ? sm.W1 : sm.W0;
-      cplx* up2 = upsample(Z2, sm.ph, Zf2, Z2, Mt, P, a.tw, a.twf, a.T, false);   // re: tau0~, im: alpha~
-      for (int pp = lane; pp < P; pp += 32) sm.Acal[pp] = up2[pp].re * up2[pp].im * sm.Acal[pp];
-      __syncwarp();
-      // ---- D6. H3 modes (symmetric), with beta tau_0 packed in the imaginary part (kk: kc is spent)
-      for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.hr[q], sm.bt0[q]);
+      // ---- D6. H3 modes (symmetric) from a transform of H3 alone: their rounding is amplified in the
+      // tau_3 term (and by up to k^2 in the translated remainder next to a), so nothing larger shares it
+      // (kk: kc is spent)
+      for (int q = lane; q < Mt; q += 32) sm.W0[q] = C(sm.hr[q], 0.0);
       __syncwarp();
       const cplx* Z3 = warp_fft(sm.W0, sm.W1, Mt, a.tw, a.T, -1);
       for (int jj = lane; jj <= 2 * M; jj += 32) {
@@ -1087,14 +1115,25 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         __syncwarp();
       }
       // ---- D10. transform (V_K A~) + i (V_H), unpack AT1 and the tau_3 Toeplitz part
-      for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(sm.Acal[pp], sm.Bcal[pp]);
+      double y2down;
+      {
+        double sk = 0.0, sh = 0.0;
+        for (int pp = lane; pp < P; pp += 32) {
+          sk += sm.Acal[pp] * sm.Acal[pp];
+          sh += sm.Bcal[pp] * sm.Bcal[pp];
+        }
+        const int ey = pack_exponent(warp_sum(sk), warp_sum(sh));   // V_H scaled to V_K A~'s size
+        const double up = ldexp(1.0, ey);
+        y2down = ldexp(1.0, -ey) / P;
+        for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(sm.Acal[pp], sm.Bcal[pp] * up);
+      }
       __syncwarp();
       const cplx* Y2 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, -1);
       for (int jj = lane; jj <= 2 * M; jj += 32) {
         const int m = jj - M;
         const cplx zp = Y2[wrapi(m, P)], zm = conj(Y2[wrapi(-m, P)]);
         const cplx y1 = 0.5 * (zp + zm) * (1.0 / P);
-        const cplx y2 = C(0.5 * (zp.im - zm.im), -0.5 * (zp.re - zm.re)) * (1.0 / P);
+        const cplx y2 = C(0.5 * (zp.im - zm.im), -0.5 * (zp.re - zm.re)) * y2down;
         const cplx e = conj(sm.ph[jj]);                                  // e^{-ima}
         cplx t3 = e * y2;
         if (translated) {

@@ -95,7 +95,8 @@ def test_modes_s_k_kprime(bie, ctx, ggq, name, surface, Np, Mt, k):
         assert err.max() <= TOL, (name, kd, int(err.argmax()), err.max())
 
 
-ROWS = [("wiggly_torus", wl.wiggly_torus(), 5, 30, 1.0), ("bean", wl.bean(), 4, 40, 2.0),
+ROWS = [("wiggly_torus", wl.wiggly_torus(), 5, 30, 1.0), ("wiggly_torus_9_30_k4", wl.wiggly_torus(), 9, 30, 4.0),
+        ("wiggly_torus_9_50_k2", wl.wiggly_torus(), 9, 50, 2.0), ("bean", wl.bean(), 4, 40, 2.0),
         ("ellipsoid123", wl.ellipsoid(1.0, 2.0, 3.0), 4, 40, 1.0)]
 
 
@@ -156,12 +157,15 @@ def paper_error(bie, ctx, ggq, example, k, kind):
                       "Kp": (bie.OP_KP_PLUS_I, 2, bie.OP_S)}[kind]
     A = bie.assemble(s, op, float(k))
     g = bie.rhs(s, rkind, SOURCE, float(k))
-    x, rep_ = bie.solve(ctx, A, g, tol=1e-13, restart=400, maxit=6000)
-    del A
+    # panel-block preconditioner (the interior problems at larger k lie near interior resonances)
+    B = bie.BlockDiag(ctx, A, 16 * Mt)
+    x, rep_ = bie.solve(ctx, A, g, tol=1e-12, restart=min(s.N, 800), maxit=20000, precond=bie.PRECOND_BLOCK,
+                        block=B, raise_on_noconv=False)
+    del A, B
     pts = _ball(center)
     u = bie.field_eval(s, rep, float(k), x, pts).cpu().numpy()
     ue = exact.point_source(float(k), pts, SOURCE)
-    return np.linalg.norm(u - ue) / len(ue), printed
+    return np.linalg.norm(u - ue) / len(ue), printed, rep_
 
 
 # every cell of the three tables whose printed error the oracle reproduces at k = 1 (the double layer
@@ -172,5 +176,5 @@ CELLS = [(e, k, kind) for e in (1, 2) for k in (1, 2, 4, 8, 16) for kind in ("S"
 
 @pytest.mark.parametrize("example,k,kind", CELLS)
 def test_paper_table_on_gpu(bie, ctx, ggq, example, k, kind):
-    E, printed = paper_error(bie, ctx, ggq, example, k, kind)
-    assert E <= 3 * printed, (example, k, kind, E, printed)
+    E, printed, rep = paper_error(bie, ctx, ggq, example, k, kind)
+    assert E <= 3 * printed, (example, k, kind, E, printed, rep["rel_residual"])
