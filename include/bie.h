@@ -79,6 +79,15 @@ typedef enum {
 bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream);
 void bie_ctx_free(bie_ctx ctx);
 const char* bie_last_error(void);
+/* Launch trace (measurement): with enable != 0 the context records CUDA events on
+ * its stream around every launch of the pair kernels (root, transform, fused),
+ * the near fill (one mark per panel group) and the far fill.
+ * bie_ctx_trace_read synchronises the stream and returns, per family (0 pair
+ * root, 1 pair transform, 2 fused pair kernel, 3 near fill, 4 far fill), the
+ * summed event time in ms and the number of marks, then clears the trace.
+ * [host] ms double[5], launches int[5].  Errors: BIE_EINVAL, BIE_ECUDA.        */
+bie_status bie_ctx_trace(bie_ctx ctx, int enable);
+bie_status bie_ctx_trace_read(bie_ctx ctx, double* ms, int* launches);
 /* Wait for all work of the context's stream; returns BIE_ECUDA on a device error,
  * BIE_EINVAL if a kernel met an invalid pair, BIE_ETIMEOUT if a bounded device
  * wait expired (both flags are cleared by the call). */

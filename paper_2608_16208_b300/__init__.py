@@ -70,6 +70,8 @@ _sig("bie_last_error", ctypes.c_char_p, [])
 _sig("bie_ctx_create", _i32, [ctypes.POINTER(_vp), _vp])
 _sig("bie_ctx_free", None, [_vp])
 _sig("bie_ctx_sync", _i32, [_vp])
+_sig("bie_ctx_trace", _i32, [_vp, _i32])
+_sig("bie_ctx_trace_read", _i32, [_vp, _vp, _vp])
 _sig("bie_surface_sample", _i32, [_vp, ctypes.POINTER(SurfaceDesc), _i32, _i32, ctypes.POINTER(QuadTables),
                                   ctypes.POINTER(_vp)])
 _sig("bie_surface_free", None, [_vp])
@@ -106,6 +108,18 @@ class Context:
 
     def sync(self):
         check(lib.bie_ctx_sync(self.h), "bie_ctx_sync")
+
+    def trace(self, enable=True):
+        """Record CUDA events around the pair, near-fill and far-fill launches of this context."""
+        check(lib.bie_ctx_trace(self.h, 1 if enable else 0), "bie_ctx_trace")
+
+    def trace_read(self):
+        """{family: (ms, launches)} of the launches recorded since the trace was switched on or last read."""
+        ms = (ctypes.c_double * 5)()
+        n = (ctypes.c_int * 5)()
+        check(lib.bie_ctx_trace_read(self.h, ms, n), "bie_ctx_trace_read")
+        names = ("pair_root", "pair_transform", "pair_fused", "near_fill", "far_fill")
+        return {names[i]: (ms[i], n[i]) for i in range(5)}
 
     def __del__(self):
         if getattr(self, "h", None):

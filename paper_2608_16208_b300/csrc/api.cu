@@ -32,9 +32,67 @@ bie_status check_device(bie_ctx ctx, const char* where) {
   return BIE_OK;
 }
 
+int trace_begin(bie_ctx ctx, int kind) {
+  if (!ctx || !ctx->trace) return -1;
+  if (!ctx->marks) ctx->marks = new std::vector<TraceMark>();
+  TraceMark m;
+  m.kind = kind;
+  if (cudaEventCreate(&m.e0) != cudaSuccess) return -1;
+  if (cudaEventCreate(&m.e1) != cudaSuccess) {
+    cudaEventDestroy(m.e0);
+    return -1;
+  }
+  cudaEventRecord(m.e0, ctx->stream);
+  ctx->marks->push_back(m);
+  return (int)ctx->marks->size() - 1;
+}
+
+void trace_end(bie_ctx ctx, int mark) {
+  if (mark < 0 || !ctx->marks || mark >= (int)ctx->marks->size()) return;
+  cudaEventRecord((*ctx->marks)[mark].e1, ctx->stream);
+}
+
+static void trace_clear(bie_ctx ctx) {
+  if (!ctx->marks) return;
+  for (TraceMark& m : *ctx->marks) {
+    cudaEventDestroy(m.e0);
+    cudaEventDestroy(m.e1);
+  }
+  ctx->marks->clear();
+}
+
 }  // namespace bie
 
 extern "C" {
+
+bie_status bie_ctx_trace(bie_ctx ctx, int enable) {
+  if (!ctx) { bie::set_error("bie_ctx_trace: NULL context"); return BIE_EINVAL; }
+  ctx->trace = enable ? 1 : 0;
+  bie::trace_clear(ctx);
+  return BIE_OK;
+}
+
+bie_status bie_ctx_trace_read(bie_ctx ctx, double* ms, int* launches) {
+  if (!ctx || !ms || !launches) { bie::set_error("bie_ctx_trace_read: invalid arguments"); return BIE_EINVAL; }
+  for (int k = 0; k < kTraceKinds; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  if (ctx->marks) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bie::cuda_fail(e, "bie_ctx_trace_read");
+    for (const TraceMark& m : *ctx->marks) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m.e0, m.e1) == cudaSuccess) {
+        ms[m.kind] += t;
+        launches[m.kind] += 1;
+      }
+    }
+  }
+  bie::trace_clear(ctx);
+  return BIE_OK;
+}
+
 
 const char* bie_last_error(void) { return bie::g_err; }
 
@@ -60,6 +118,8 @@ bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream) {
 void bie_ctx_free(bie_ctx ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  bie::trace_clear(ctx);
+  delete ctx->marks;
   cudaFree(ctx->pair_scratch);
   cudaFree(ctx->pair_records);
   cudaFree(ctx->d_status);

@@ -245,6 +245,7 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
     if (st != BIE_OK) break;
     const cplx* WS = (kernels & BIE_KERNEL_S) ? W : nullptr;
     const cplx* WK = dl ? W + (nk - 1) * a.weights_stride : nullptr;
+    const int tm = trace_begin(ctx, kTraceNearFill);
     for (int jj = 0; jj < nj; ++jj) {
       const int64_t off = (int64_t)jj * panel_pairs * Mt;
       dim3 grid(16 * Mt, 3);
@@ -255,6 +256,7 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
         near_fill_kernel<false><<<grid, 256, 0, st0>>>(s->Np, Mt, s->sp.periodic, j0 + jj, sS, sK, s->near_coef, s->near_coef_dw,
                                                        WS ? WS + off : nullptr, WK ? WK + off : nullptr, jac, o);
     }
+    trace_end(ctx, tm);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = cuda_fail(e, "near_fill_kernel"); break; }
     if (host_band) {
@@ -363,7 +365,9 @@ bie_status bie_assemble(bie_ctx ctx, bie_surface s, int op_flags, double k, doub
   fa.A = (cplx*)A_out;
   const int64_t row_tiles = (s->N + kFarRows - 1) / kFarRows;
   dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)(row_tiles < 65535 ? row_tiles : 65535));
+  const int tm = trace_begin(ctx, kTraceFarFill);
   far_fill_kernel<<<grid, 256, 0, ctx->stream>>>(fa);
+  trace_end(ctx, tm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "far_fill_kernel");
   unsigned kernels = 0;

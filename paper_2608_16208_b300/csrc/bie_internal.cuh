@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/bie.h"
 
 namespace bie {
@@ -438,11 +440,20 @@ static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cpl
 }  // namespace bie
 
 // Opaque handles (host side)
+// kernel families timed by the context's launch trace (bie_ctx_trace)
+enum { kTracePairRoot = 0, kTracePairTransform = 1, kTracePairFused = 2, kTraceNearFill = 3, kTraceFarFill = 4,
+       kTraceKinds = 5 };
+struct TraceMark {
+  int kind;
+  cudaEvent_t e0, e1;
+};
 struct bie_ctx_s {
   cudaStream_t stream;
   int device;
   int sms;
   int* d_status;       // device status word (error flags from kernels)
+  int trace = 0;       // record CUDA events around the pair, near-fill and far-fill launches
+  std::vector<TraceMark>* marks = nullptr;
   // pair-pipeline work buffers of this context (grown on demand, freed by bie_ctx_free): the
   // per-warp recurrence scratch of the fused kernels and the per-pair records of the split launch
   double* pair_scratch = nullptr;
@@ -479,6 +490,9 @@ struct bie_surface_s {
 struct bie_net_infer_s;
 
 namespace bie {
+// launch trace: trace_begin returns an index (or -1 when tracing is off), trace_end records the end
+int trace_begin(bie_ctx ctx, int kind);
+void trace_end(bie_ctx ctx, int mark);
 void set_error(const char* fmt, ...);
 bie_status cuda_fail(cudaError_t e, const char* where);
 // BIE_OK if the context's device is the current one, else BIE_EINVAL naming the call

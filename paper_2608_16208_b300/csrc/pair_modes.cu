@@ -1371,9 +1371,13 @@ static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
   for (int64_t c0 = 0; c0 < a.n_pairs; c0 += chunk) {
     const int64_t cn = std::min(chunk, a.n_pairs - c0);
     const int64_t br = std::max<int64_t>(1, std::min<int64_t>((int64_t)s->ctx->sms * per_r, (cn + 127) / 128));
+    int tm = trace_begin(s->ctx, kTracePairRoot);
     pair_root_kernel<<<(unsigned)br, 128, 0, st>>>(a, c0, cn);
+    trace_end(s->ctx, tm);
     const int64_t bt = std::max<int64_t>(1, std::min<int64_t>((int64_t)s->ctx->sms * per_t, (cn + 32 * wpb - 1) / (32 * wpb)));
+    tm = trace_begin(s->ctx, kTracePairTransform);
     pair_transform_kernel<<<(unsigned)bt, 32 * wpb, smem, st>>>(a, c0, cn);
+    trace_end(s->ctx, tm);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair kernels (split launch)");
@@ -1409,7 +1413,9 @@ bie_status launch_pairs(bie_surface s, PairArgs& a) {
     if (rs != BIE_OK) return rs;
   }
   a.scratch = s->ctx->pair_scratch;
+  const int tm = trace_begin(s->ctx, kTracePairFused);
   kern<<<(unsigned)blocks, 32 * wpb, smem, s->ctx->stream>>>(a);
+  trace_end(s->ctx, tm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "pair_kernel launch");
   return BIE_OK;
