@@ -331,6 +331,25 @@ def run_gpu(args):
     torch.cuda.synchronize()
     pk_ms = float(np.mean([a.elapsed_time(b) for a, b in pk_events]))
     pk_pairs = rows_all.numel()
+    # the same launch with the single layer's transforms in FP64 (context option): what the double-word
+    # arithmetic buys, on the same pairs
+    ctx.set_option(bie.OPT_FP64_TRANSFORMS, 1)
+    bie.kernel_modes(surf, bie.KERNEL_S, k, rows_all, srcs_all, out=modes)
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bie.kernel_modes(surf, bie.KERNEL_S, k, rows_all, srcs_all, out=modes)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f64_ms = e0.elapsed_time(e1)
+    ctx.set_option(bie.OPT_FP64_TRANSFORMS, 0)
+    pick64 = np.unique(wl.Stream(11, 5).integers(0, pk_pairs - 1, 128))
+    pick64_d = torch.from_numpy(pick64).to(dev)
+    f64_rows, f64_srcs = rows_all[pick64_d].cpu().numpy(), srcs_all[pick64_d].cpu().numpy()
+    f64_got = modes[pick64_d, 0].cpu().numpy()
+    # and again in double words, so that the accuracy sample below comes from the timed arithmetic
+    bie.kernel_modes(surf, bie.KERNEL_S, k, rows_all, srcs_all, out=modes)
+    torch.cuda.synchronize()
     # accuracy of the timed launch: 256 seeded pairs of its output against the oracle, one by one
     pick = np.unique(wl.Stream(11, 4).integers(0, pk_pairs - 1, 256))
     pick_d = torch.from_numpy(pick).to(dev)
@@ -376,6 +395,7 @@ def run_gpu(args):
     h2d = 8 * (3 * 16 * 16 * 2 + 32) + 5 * 8 * len(c["surface"].get("terms", []))
 
     acc = accuracy_vs_oracle(c, acc_rows, acc_srcs, acc_got)
+    acc64 = accuracy_vs_oracle(c, f64_rows, f64_srcs, f64_got)
 
     # time to a 1e-8 residual: FP64 vs the mixed solves, on this workload (4 plane waves + a point
     # source) and on the bumpy surface at k = 20 (N = 49,152; plane wave + point source)
@@ -427,6 +447,11 @@ def run_gpu(args):
                                        "single-threaded processes (%s)" % (cpu_n, cpu_dt, cpu_cores, cpu_model)},
             "precision": PRECISION,
             "accuracy_vs_oracle": acc,
+            "fp64_only": {"pairs_per_s": pk_pairs / (f64_ms / 1000.0), "ms": f64_ms, "pairs": pk_pairs,
+                          "double_word_pairs_per_s": pk_pairs / (pk_ms / 1000.0),
+                          "speedup_of_double_words": f64_ms / pk_ms, "accuracy_vs_oracle": acc64,
+                          "path": "the same kernel-modes launch with the transforms, upsampling, products and "
+                                  "unpacking in FP64 (BIE_OPT_FP64_TRANSFORMS)"},
             "solve": solve,
             "batch": batch,
             "rows": rows,

@@ -79,6 +79,16 @@ typedef enum {
 bie_status bie_ctx_create(bie_ctx* out, void* cuda_stream);
 void bie_ctx_free(bie_ctx ctx);
 const char* bie_last_error(void);
+/* Options of a context.  BIE_OPT_FP64_TRANSFORMS (value 0 or 1, default 0): the
+ * single layer's transforms, upsampling, products and unpacking in FP64 instead of
+ * double-word FP32 arithmetic (about 48 significant bits; both stay within the
+ * 1e-12 per-pair bound), in bie_kernel_modes and the assembly calls; a measure of
+ * what the narrower arithmetic buys.  The batch scheduler, the allocation-free
+ * entry and the double layer's fused kernel are not affected.
+ * Errors: BIE_EINVAL.                                                          */
+#define BIE_OPT_FP64_TRANSFORMS 1
+bie_status bie_ctx_set_option(bie_ctx ctx, int option, int value);
+
 /* Launch trace (measurement): with enable != 0 the context records CUDA events on
  * its stream around every launch of the pair kernels (root, transform, fused),
  * the near fill (one mark per panel group) and the far fill.

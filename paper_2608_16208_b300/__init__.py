@@ -71,6 +71,8 @@ _sig("bie_ctx_create", _i32, [ctypes.POINTER(_vp), _vp])
 _sig("bie_ctx_free", None, [_vp])
 _sig("bie_ctx_sync", _i32, [_vp])
 _sig("bie_ctx_trace", _i32, [_vp, _i32])
+_sig("bie_ctx_set_option", _i32, [_vp, _i32, _i32])
+OPT_FP64_TRANSFORMS = 1
 _sig("bie_ctx_trace_read", _i32, [_vp, _vp, _vp])
 _sig("bie_surface_sample", _i32, [_vp, ctypes.POINTER(SurfaceDesc), _i32, _i32, ctypes.POINTER(QuadTables),
                                   ctypes.POINTER(_vp)])
@@ -108,6 +110,9 @@ class Context:
 
     def sync(self):
         check(lib.bie_ctx_sync(self.h), "bie_ctx_sync")
+
+    def set_option(self, option, value):
+        check(lib.bie_ctx_set_option(self.h, int(option), int(value)), "bie_ctx_set_option")
 
     def trace(self, enable=True):
         """Record CUDA events around the pair, near-fill and far-fill launches of this context."""

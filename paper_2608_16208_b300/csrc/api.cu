@@ -65,6 +65,14 @@ static void trace_clear(bie_ctx ctx) {
 
 extern "C" {
 
+bie_status bie_ctx_set_option(bie_ctx ctx, int option, int value) {
+  if (!ctx) { bie::set_error("bie_ctx_set_option: NULL context"); return BIE_EINVAL; }
+  switch (option) {
+    case BIE_OPT_FP64_TRANSFORMS: ctx->fp64_transforms = value ? 1 : 0; return BIE_OK;
+    default: bie::set_error("bie_ctx_set_option: unknown option %d", option); return BIE_EINVAL;
+  }
+}
+
 bie_status bie_ctx_trace(bie_ctx ctx, int enable) {
   if (!ctx) { bie::set_error("bie_ctx_trace: NULL context"); return BIE_EINVAL; }
   ctx->trace = enable ? 1 : 0;

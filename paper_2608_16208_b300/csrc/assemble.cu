@@ -221,7 +221,8 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
     }
   }
   const cplx sS = ws * (0.5 * s->h), sK = wk * (0.5 * s->h);
-  const bool dw = kernels == BIE_KERNEL_S;   // single layer alone: double-word weights and fold
+  // single layer alone: double-word weights and fold (unless the context runs the transforms in FP64)
+  const bool dw = kernels == BIE_KERNEL_S && !ctx->fp64_transforms;
   for (int j0 = 0, gi = 0; j0 < s->Np && st == BIE_OK; j0 += group, ++gi) {
     const int nj = (j0 + group <= s->Np) ? group : s->Np - j0;
     const int slot = gi & 1;

@@ -453,6 +453,7 @@ struct bie_ctx_s {
   int sms;
   int* d_status;       // device status word (error flags from kernels)
   int trace = 0;       // record CUDA events around the pair, near-fill and far-fill launches
+  int fp64_transforms = 0;   // BIE_OPT_FP64_TRANSFORMS
   std::vector<TraceMark>* marks = nullptr;
   // pair-pipeline work buffers of this context (grown on demand, freed by bie_ctx_free): the
   // per-warp recurrence scratch of the fused kernels and the per-pair records of the split launch

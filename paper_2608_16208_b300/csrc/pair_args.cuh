@@ -35,6 +35,7 @@ struct PairArgs {
   int64_t out_base, out_mod;      // output slot of pair p: (out_base + p) % out_mod when out_mod > 0
   int64_t w_ld;                   // complex elements between consecutive weight rows (Mt by default)
   int weights_dw;                 // single layer: weights as double words (re.h, re.l, im.h, im.l)
+  int fp64_transforms;            // single layer, split launch: transforms in FP64 instead of double words
   int* status;
   // single layer, split launch: one record per pair of the chunk, written by the root kernel
   double* rec_hdr;                // [pair][8]: a, e^{-b}, 1 - e^{-b}, sin(a/2), cos(a/2), valid

@@ -449,21 +449,85 @@ __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, c
 }
 
 // ------------------------------------------------------------------ phase D, single layer alone
+// Arithmetic of the single layer's transforms: double words on the FP32 pipe (ArDW, the default) or
+// FP64 throughout (ArF64, a context option that measures what the narrower arithmetic buys).  Both
+// hold a complex value in 16 bytes and a real one in 8, so the records and shared memory are shared.
+struct ArDW {
+  using C = float4;
+  using R = float2;
+  static __device__ __forceinline__ R rfrom(double v) { return dw_from(v); }
+  static __device__ __forceinline__ double rto(R v) { return dw_to(v); }
+  static __device__ __forceinline__ cplx cto(C v) { return dwc_to(v); }
+  static __device__ __forceinline__ C mul(C x, C y) { return dwc_mul(x, y); }
+  static __device__ __forceinline__ C mulr(C x, R r) { return dwc_mulr(x, r); }
+  static __device__ __forceinline__ C conjg(C x) { return dwc_conj(x); }
+  static __device__ __forceinline__ C add(C x, C y) { return dwc_add(x, y); }
+  static __device__ __forceinline__ C half(C x) { return dwc_scale2(x, 0.5f); }
+  static __device__ __forceinline__ C zero() { return dwc_zero(); }
+  static __device__ __forceinline__ C mk(R re, R im) { return mkc(re, im); }
+  static __device__ __forceinline__ R re(C x) { return cre(x); }
+  static __device__ __forceinline__ R im(C x) { return cim(x); }
+  static __device__ __forceinline__ R rzero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ R rmul(R x, R y) { return dw_mul(x, y); }
+  static __device__ __forceinline__ R radd(R x, R y) { return dw_add(x, y); }
+  static __device__ __forceinline__ R rsub(R x, R y) { return dw_sub(x, y); }
+  static __device__ __forceinline__ R rscale(R x, int e) { return dw_scale2(x, ldexpf(1.f, e)); }
+  static __device__ __forceinline__ C imscale(C x, int e) {
+    const float sc = ldexpf(1.f, e);
+    return make_float4(x.x, x.y, x.z * sc, x.w * sc);
+  }
+  static __device__ __forceinline__ double lead(R x) { return (double)x.x; }
+  static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { dw_sincos(x, s, c); }
+  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign) {
+    return warp_fft_dw(x, y, n, a.twf, a.T, sign);
+  }
+};
+struct ArF64 {
+  using C = cplx;
+  using R = double;
+  static __device__ __forceinline__ R rfrom(double v) { return v; }
+  static __device__ __forceinline__ double rto(R v) { return v; }
+  static __device__ __forceinline__ cplx cto(C v) { return v; }
+  static __device__ __forceinline__ C mul(C x, C y) { return x * y; }
+  static __device__ __forceinline__ C mulr(C x, R r) { return x * r; }
+  static __device__ __forceinline__ C conjg(C x) { return conj(x); }
+  static __device__ __forceinline__ C add(C x, C y) { return x + y; }
+  static __device__ __forceinline__ C half(C x) { return 0.5 * x; }
+  static __device__ __forceinline__ C zero() { return bie::C(0.0); }
+  static __device__ __forceinline__ C mk(R re, R im) { return bie::C(re, im); }
+  static __device__ __forceinline__ R re(C x) { return x.re; }
+  static __device__ __forceinline__ R im(C x) { return x.im; }
+  static __device__ __forceinline__ R rzero() { return 0.0; }
+  static __device__ __forceinline__ R rmul(R x, R y) { return x * y; }
+  static __device__ __forceinline__ R radd(R x, R y) { return x + y; }
+  static __device__ __forceinline__ R rsub(R x, R y) { return x - y; }
+  static __device__ __forceinline__ R rscale(R x, int e) { return ldexp(x, e); }
+  static __device__ __forceinline__ C imscale(C x, int e) { return bie::C(x.re, ldexp(x.im, e)); }
+  static __device__ __forceinline__ double lead(R x) { return x; }
+  static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { sincos(x, s, c); }
+  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign) {
+    return warp_fft(x, y, n, a.tw, a.T, sign);
+  }
+};
+
 // The same steps as the general phase D below, with every transform, the upsampling, the products
-// and the unpacking in double-word arithmetic (dw.cuh); FP64 for the samples and the outputs.
-//   E       [pair][33] double-word e^{i l a} (l < 32) and e^{32 i a} of the batch (phase B)
-//   Ab      A_m as double words: A_m of pair j at Ab[j a_ps + m a_ms]
+// and the unpacking in the arithmetic Ar; FP64 for the samples and the outputs.
+//   E       [pair][33] e^{i l a} (l < 32) and e^{32 i a} of the batch (phase B), in Ar's complex form
+//   Ab      A_m in Ar's real form: A_m of pair j at Ab[j a_ps + m a_ms]
 //   R2      rho^2 on the ring, [pair][Mt] (phase A, with the cancellation-free differences)
-__device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const float2* Ab, int a_ps, int a_ms,
-                                               const float4* E, const double* R2, const PairInfo& mine,
-                                               unsigned valid_mask, int64_t p0, int nb) {
+template <class Ar>
+__device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm, const typename Ar::R* Ab, int a_ps,
+                                               int a_ms, const typename Ar::C* E, const double* R2,
+                                               const PairInfo& mine, unsigned valid_mask, int64_t p0, int nb) {
+  using Cx = typename Ar::C;
+  using Rx = typename Ar::R;
   const int lane = threadIdx.x & 31;
   const int Mt = a.Mt, M = a.M, P = a.P, L = a.L;
-  float4* W0 = reinterpret_cast<float4*>(sm.W0);
-  float4* W1 = reinterpret_cast<float4*>(sm.W1);
-  float2* Acal = reinterpret_cast<float2*>(sm.Acal);
-  const float2 invMt = dw_from(1.0 / Mt);
-  const float2 ratio = dw_from((double)Mt / P);   // e^{ija}/Mt -> e^{ija}/P
+  Cx* W0 = reinterpret_cast<Cx*>(sm.W0);
+  Cx* W1 = reinterpret_cast<Cx*>(sm.W1);
+  Rx* Acal = reinterpret_cast<Rx*>(sm.Acal);
+  const Rx invMt = Ar::rfrom(1.0 / Mt);
+  const Rx ratio = Ar::rfrom((double)Mt / P);   // e^{ija}/Mt -> e^{ija}/P
   int acal_next = -1;   // pair whose circulant transform already sits in Acal
   for (int pi = 0; pi < nb; ++pi) {
     const PairInfo pr = bcast(mine, pi);
@@ -477,15 +541,15 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     }
     const double* r2p = R2 + pi * Mt;
     // ---- phases e^{ija}/Mt, j = -M..M: lane l starts from e^{i l a}, steps of e^{32 i a}
-    float4* ph = reinterpret_cast<float4*>(sm.ph);
+    Cx* ph = reinterpret_cast<Cx*>(sm.ph);
     {
-      float4 e = E[pi * 33 + lane];
-      const float4 step = E[pi * 33 + 32];
+      Cx e = E[pi * 33 + lane];
+      const Cx step = E[pi * 33 + 32];
       for (int j = lane; j <= M; j += 32) {
-        const float4 es = dwc_mulr(e, invMt);
+        const Cx es = Ar::mulr(e, invMt);
         ph[M + j] = es;
-        ph[M - j] = dwc_conj(es);
-        e = dwc_mul(e, step);
+        ph[M - j] = Ar::conjg(es);
+        e = Ar::mul(e, step);
       }
     }
     __syncwarp();
@@ -494,15 +558,15 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     if (acal_next != pi) {
       for (int pp = lane; pp < P; pp += 32) {
         const int dd = pp <= P / 2 ? pp : P - pp;
-        W1[pp] = mkc(dd <= L ? Ab[pi * a_ps + dd * a_ms] : make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+        W1[pp] = Ar::mk(dd <= L ? Ab[pi * a_ps + dd * a_ms] : Ar::rzero(), Ar::rzero());
       }
       __syncwarp();
-      const float4* Af = warp_fft_dw(W1, W0, P, a.twf, a.T, -1);
-      for (int pp = lane; pp < P; pp += 32) Acal[pp] = cre(Af[pp]);
+      const Cx* Af = Ar::fft(W1, W0, P, a, -1);
+      for (int pp = lane; pp < P; pp += 32) Acal[pp] = Ar::re(Af[pp]);
     }
     __syncwarp();
-    // ---- samples: F + i cos(k rho) and sin(k rho)/rho, as double words
-    float2* snw = reinterpret_cast<float2*>(sm.sn);
+    // ---- samples: F + i cos(k rho) and sin(k rho)/rho
+    Rx* snw = reinterpret_cast<Rx*>(sm.sn);
     for (int q = lane; q < Mt; q += 32) {
       const double thq = a.thg[3 * q];
       const double r2 = r2p[q];
@@ -512,26 +576,26 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       const double sp = fabs(dq) < 0.1 ? sin(0.5 * dq) : a.thg[3 * q + 1] * pr.cha - a.thg[3 * q + 2] * pr.sha;
       const double sv = pr.om * pr.om + 4 * pr.qb * sp * sp;
       const double F = sqrt(sv) * rinv;
-      float2 skr, ckr;
-      dw_sincos(a.k * rho, &skr, &ckr);
-      W0[q] = mkc(dw_from(F), ckr);
-      snw[q] = dw_mul(skr, dw_from(rinv));
+      Rx skr, ckr;
+      Ar::sincosr(a.k * rho, &skr, &ckr);
+      W0[q] = Ar::mk(Ar::rfrom(F), ckr);
+      snw[q] = Ar::rmul(skr, Ar::rfrom(rinv));
     }
     __syncwarp();
     // ---- modes of F and cos(k rho); upsample onto the shifted P grid
-    float4* Z1 = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
-    float4* X = (Z1 == W0) ? W1 : W0;
-    for (int pp = lane; pp < P; pp += 32) X[pp] = dwc_zero();
+    Cx* Z1 = Ar::fft(W0, W1, Mt, a, -1);
+    Cx* X = (Z1 == W0) ? W1 : W0;
+    for (int pp = lane; pp < P; pp += 32) X[pp] = Ar::zero();
     __syncwarp();
     for (int jj = lane; jj <= 2 * M; jj += 32) {
       const int jv = jj - M;
-      float4 z = dwc_mul(phase(jj), Z1[wrap1(jv, Mt)]);
-      if (jv == M || jv == -M) z = dwc_scale2(z, 0.5f);
+      Cx z = Ar::mul(phase(jj), Z1[wrap1(jv, Mt)]);
+      if (jv == M || jv == -M) z = Ar::half(z);
       X[wrap1(jv, P)] = z;
     }
     __syncwarp();
-    float4* up1 = warp_fft_dw(X, Z1, P, a.twf, a.T, +1);   // re: F~, im: C~
-    float4* uf = (up1 == W0) ? W1 : W0;
+    Cx* up1 = Ar::fft(X, Z1, P, a, +1);   // re: F~, im: C~
+    Cx* uf = (up1 == W0) ? W1 : W0;
     // ---- U = F~ C~ Acal in the real part, the next valid pair's circulant in the imaginary part.
     // Each part comes out of the shared transform with an error in proportion to the other's size
     // (the product is 10^3 times the circulant next to a pole), so the circulant is scaled by an
@@ -542,12 +606,13 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     float su = 0.f, sa = 0.f;
     for (int pp = lane; pp < P; pp += 32) {
       const int dd = pp <= P / 2 ? pp : P - pp;
-      const float4 u = up1[pp];
-      const float2 prod = dw_mul(dw_mul(cre(u), cim(u)), Acal[pp]);
-      const float2 an = (pack && dd <= L) ? Ab[nxt * a_ps + dd * a_ms] : make_float2(0.f, 0.f);
-      su = fmaf(prod.x, prod.x, su);
-      sa = fmaf(an.x, an.x, sa);
-      uf[pp] = mkc(prod, an);
+      const Cx u = up1[pp];
+      const Rx prod = Ar::rmul(Ar::rmul(Ar::re(u), Ar::im(u)), Acal[pp]);
+      const Rx an = (pack && dd <= L) ? Ab[nxt * a_ps + dd * a_ms] : Ar::rzero();
+      const float pf = (float)Ar::lead(prod), af = (float)Ar::lead(an);
+      su = fmaf(pf, pf, su);
+      sa = fmaf(af, af, sa);
+      uf[pp] = Ar::mk(prod, an);
     }
     for (int o = 16; o; o >>= 1) {
       su += __shfl_xor_sync(0xffffffffu, su, o);
@@ -556,61 +621,56 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     int pe = 0;   // circulant scale 2^pe
     if (pack && sa > 0.f && su > 0.f) pe = max(-60, min(60, (int)rintf(0.5f * log2f(su / sa))));
     if (pe) {
-      const float sc = ldexpf(1.f, pe);
       __syncwarp();
-      for (int pp = lane; pp < P; pp += 32) {
-        uf[pp].z *= sc;
-        uf[pp].w *= sc;
-      }
+      for (int pp = lane; pp < P; pp += 32) uf[pp] = Ar::imscale(uf[pp], pe);
     }
     __syncwarp();
-    const float4* Yf = warp_fft_dw(uf, up1, P, a.twf, a.T, -1);
+    const Cx* Yf = Ar::fft(uf, up1, P, a, -1);
     // ---- kernel modes kc_m = e^{-ima} (Re-part transform)_m / P, m = -M..M, written straight to the
     // modes output and to the free buffer in the input order of the weights' inverse transform
     // (q = m mod Mt; q = M holds the mean of m = -M and m = M)
-    float4* Wi = (Yf == W0) ? W1 : W0;
+    Cx* Wi = (Yf == W0) ? W1 : W0;
     double* out = a.modes_out ? a.modes_out + p * 2 * (Mt + 1) : nullptr;
     auto kc_of = [&](int jj) {
       const int m = jj - M;
-      const float4 zp = Yf[wrap1(m, P)], zm = dwc_conj(Yf[wrap1(-m, P)]);
-      return dwc_mul(dwc_mulr(dwc_conj(phase(jj)), ratio), dwc_scale2(dwc_add(zp, zm), 0.5f));
+      const Cx zp = Yf[wrap1(m, P)], zm = Ar::conjg(Yf[wrap1(-m, P)]);
+      return Ar::mul(Ar::mulr(Ar::conjg(phase(jj)), ratio), Ar::half(Ar::add(zp, zm)));
     };
     for (int jj = lane; jj <= 2 * M; jj += 32) {
-      const float4 kv = kc_of(jj);
+      const Cx kv = kc_of(jj);
       if (out) {
-        const cplx c = dwc_to(kv);
+        const cplx c = Ar::cto(kv);
         out[2 * jj] = c.re;
         out[2 * jj + 1] = c.im;
       }
       if (a.weights_out) {
         const int m = jj - M;
-        if (jj == 0) Wi[M] = dwc_scale2(dwc_add(kv, kc_of(2 * M)), 0.5f);
+        if (jj == 0) Wi[M] = Ar::half(Ar::add(kv, kc_of(2 * M)));
         else if (jj < 2 * M) Wi[m < 0 ? m + Mt : m] = kv;
       }
     }
     if (pack) {
-      const float unsc = ldexpf(0.5f, -pe);
       for (int pp = lane; pp < P; pp += 32) {
-        const float4 zp = Yf[pp], zm = dwc_conj(Yf[pp == 0 ? 0 : P - pp]);
-        Acal[pp] = dw_scale2(dw_sub(cim(zp), cim(zm)), unsc);
+        const Cx zp = Yf[pp], zm = Ar::conjg(Yf[pp == 0 ? 0 : P - pp]);
+        Acal[pp] = Ar::rscale(Ar::rsub(Ar::im(zp), Ar::im(zm)), -pe - 1);
       }
       acal_next = nxt;
     }
     __syncwarp();
     // ---- Parseval weights: inverse transform of the kernel modes, plus sin(k rho)/(rho Mt)
     if (a.weights_out) {
-      const float4* Wt = warp_fft_dw(Wi, (Wi == W0) ? W1 : W0, Mt, a.twf, a.T, +1);
+      const Cx* Wt = Ar::fft(Wi, (Wi == W0) ? W1 : W0, Mt, a, +1);
       cplx* wout = a.weights_out + p * a.w_ld;
-      if (a.weights_dw) {
-        float4* wo = reinterpret_cast<float4*>(wout);
+      if (a.weights_dw) {   // (double-word arithmetic only)
+        Cx* wo = reinterpret_cast<Cx*>(wout);
         for (int q = lane; q < Mt; q += 32) {
-          const float4 w = Wt[q];
-          wo[q] = mkc(dw_mul(cre(w), invMt), dw_mul(dw_add(cim(w), snw[q]), invMt));
+          const Cx w = Wt[q];
+          wo[q] = Ar::mk(Ar::rmul(Ar::re(w), invMt), Ar::rmul(Ar::radd(Ar::im(w), snw[q]), invMt));
         }
       } else {
         for (int q = lane; q < Mt; q += 32) {
-          const cplx w = dwc_to(Wt[q]) * (1.0 / Mt);
-          wout[q] = C(w.re, w.im + dw_to(snw[q]) * (1.0 / Mt));
+          const cplx w = Ar::cto(Wt[q]) * (1.0 / Mt);
+          wout[q] = C(w.re, w.im + Ar::rto(snw[q]) * (1.0 / Mt));
         }
       }
       __syncwarp();
@@ -618,12 +678,12 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
     // ---- modes K_m = kc_m + i <sin(k rho)/rho>_m: the smooth part added to the kernel part in out
     // (each entry by the lane that wrote it)
     if (out) {
-      for (int q = lane; q < Mt; q += 32) W0[q] = mkc(snw[q], make_float2(0.f, 0.f));
+      for (int q = lane; q < Mt; q += 32) W0[q] = Ar::mk(snw[q], Ar::rzero());
       __syncwarp();
-      const float4* Sf = warp_fft_dw(W0, W1, Mt, a.twf, a.T, -1);
+      const Cx* Sf = Ar::fft(W0, W1, Mt, a, -1);
       for (int mm = lane; mm <= 2 * M; mm += 32) {
         const int m = mm - M;
-        cplx sv = dwc_to(Sf[wrap1(m, Mt)]) * (1.0 / Mt);
+        cplx sv = Ar::cto(Sf[wrap1(m, Mt)]) * (1.0 / Mt);
         if (m == M || m == -M) sv = 0.5 * sv;
         out[2 * mm] -= sv.im;
         out[2 * mm + 1] += sv.re;
@@ -730,19 +790,23 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
       mine.om = -expm1(-mine.b);
       sincos(0.5 * mine.a, &mine.sha, &mine.cha);
       if (!wantK) {
-        // e^{i l a} for l = 0..31 by rotation and e^{32 i a} directly, as double words ([pair][33])
+        // e^{i l a} for l = 0..31 by rotation and e^{32 i a} directly ([pair][33]), as double words or
+        // (FP64 transforms) as complex doubles
         float4* El = E + lane * 33;
         const cplx e1 = C(mine.cha * mine.cha - mine.sha * mine.sha, 2 * mine.sha * mine.cha);
         cplx e = C(1.0);
         for (int l = 0; l < 32; ++l) {
-          El[l] = dwc_from(e);
+          if (a.fp64_transforms) reinterpret_cast<cplx*>(El)[l] = e;
+          else El[l] = dwc_from(e);
           e = e * e1;
         }
-        El[32] = dwc_from(cexpi(32.0 * mine.a));
+        if (a.fp64_transforms) reinterpret_cast<cplx*>(El)[32] = cexpi(32.0 * mine.a);
+        else El[32] = dwc_from(cexpi(32.0 * mine.a));
       }
       // FP64 recurrences (Miller runs up to L + 20/b steps: its rounding would add up in double words);
-      // the single layer keeps A_m as double words for its transforms
-      a_modes_lane(mine.b, L, a.rec, a.rec_len, Ab + lane * a_ps, wantK ? scrD + lane : nullptr, a_ms, !wantK);
+      // the single layer keeps A_m as double words for its transforms (or FP64 with FP64 transforms)
+      a_modes_lane(mine.b, L, a.rec, a.rec_len, Ab + lane * a_ps, wantK ? scrD + lane : nullptr, a_ms,
+                   !wantK && !a.fp64_transforms);
     }
     __syncwarp();
 }
@@ -761,7 +825,8 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
     double* R2 = wantK ? nullptr : scrD + 2 * 33 * 32;
     front_batch<kWithK>(a, sm, p0, nb, R2, reinterpret_cast<float4*>(scrD), scrA, 1, 32, scrD, mine, valid_mask);
     if constexpr (!kWithK) {
-      phase_d_single(a, sm, reinterpret_cast<const float2*>(scrA), 1, 32, reinterpret_cast<const float4*>(scrD), R2, mine, valid_mask, p0, nb);
+      phase_d_single<ArDW>(a, sm, reinterpret_cast<const float2*>(scrA), 1, 32, reinterpret_cast<const float4*>(scrD),
+                           R2, mine, valid_mask, p0, nb);
     } else {
     // ---------------- D. per pair (warp)
     // The transforms this layer shares with the single layer (the samples F + i cos, their
@@ -1172,7 +1237,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const __gr
 // memory) and writes one record per pair; the transform kernel runs phase D on the records (double
 // words, shared-memory FFTs).  Each kernel gets its own register and occupancy budget.  Both cover
 // the pairs [c0, c0 + cn) of the launch; the record of pair p is p - c0.
-__global__ void __launch_bounds__(128) pair_root_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
+__global__ void __launch_bounds__(128, 4) pair_root_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1196,6 +1261,7 @@ __global__ void __launch_bounds__(128) pair_root_kernel(const __grid_constant__ 
   }
 }
 
+template <class Ar>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
     pair_transform_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
   extern __shared__ double smem[];
@@ -1219,7 +1285,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
       mine.valid = h[5] != 0.0;
     }
     const unsigned vm = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
-    phase_d_single(a, sm, reinterpret_cast<const float2*>(a.rec_A + r0 * (L + 1)), L + 1, 1, a.rec_E + r0 * 33,
+    phase_d_single<Ar>(a, sm, reinterpret_cast<const typename Ar::R*>(a.rec_A + r0 * (L + 1)), L + 1, 1,
+                       reinterpret_cast<const typename Ar::C*>(a.rec_E + r0 * 33),
                    a.rec_R2 + r0 * Mt, mine, vm, p0, nb);
   }
 }
@@ -1268,6 +1335,7 @@ PairArgs make_pair_args(bie_surface s, double k, unsigned kernels) {
   a.kernels = (int)kernels;
   const bool withK = kernels & (BIE_KERNEL_K | BIE_KERNEL_KP);
   a.kprime = (kernels & BIE_KERNEL_KP) ? 1 : 0;
+  a.fp64_transforms = s->ctx->fp64_transforms;
   a.out_nk = ((kernels & BIE_KERNEL_S) ? 1 : 0) + (withK ? 1 : 0);
   a.out_k0 = 0;
   a.P = (withK ? 4 : 3) * s->Mt;
@@ -1351,22 +1419,22 @@ static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_r, pair_root_kernel, 128, 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy(pair_root_kernel)");
   if (per_r < 1) per_r = 1;
-  // transform kernel: the CTA shape (1, 2 or 4 warps) with the most resident warps
+  // transform kernel (double words, or FP64 when the context asks): the CTA shape (1, 2 or 4 warps) with
+  // the most resident warps
+  auto tkern = a.fp64_transforms ? pair_transform_kernel<ArF64> : pair_transform_kernel<ArDW>;
   const size_t per_w = smem_doubles(a.Mt, a.P, a.L, false) * sizeof(double);
   int wpb = 0, best_w = 0, per_t = 0;
   for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
     if (per_w * w > kSmemLimit) continue;
-    if (cudaFuncSetAttribute(pair_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_w * w)) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(tkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_w * w)) != cudaSuccess)
       continue;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_transform_kernel, 32 * w, per_w * w) != cudaSuccess)
-      continue;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tkern, 32 * w, per_w * w) != cudaSuccess) continue;
     if (nb * w > best_w) { best_w = nb * w; wpb = w; per_t = nb; }
   }
   if (wpb < 1) { set_error("pair transform kernel: Mth = %d needs more shared memory than a CTA has", a.Mt); return BIE_EUNSUPPORTED; }
   const size_t smem = per_w * wpb;
-  e = cudaFuncSetAttribute(pair_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(tkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(pair_transform_kernel)");
   for (int64_t c0 = 0; c0 < a.n_pairs; c0 += chunk) {
     const int64_t cn = std::min(chunk, a.n_pairs - c0);
@@ -1376,7 +1444,7 @@ static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
     trace_end(s->ctx, tm);
     const int64_t bt = std::max<int64_t>(1, std::min<int64_t>((int64_t)s->ctx->sms * per_t, (cn + 32 * wpb - 1) / (32 * wpb)));
     tm = trace_begin(s->ctx, kTracePairTransform);
-    pair_transform_kernel<<<(unsigned)bt, 32 * wpb, smem, st>>>(a, c0, cn);
+    tkern<<<(unsigned)bt, 32 * wpb, smem, st>>>(a, c0, cn);
     trace_end(s->ctx, tm);
   }
   e = cudaGetLastError();
@@ -1521,6 +1589,7 @@ extern "C" bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsig
     st.ready = true;
   }
   PairArgs a = make_pair_args(s, k, kernels);
+  a.fp64_transforms = 0;   // the fused kernel's single layer runs in double words
   a.rows = pair_row;
   a.srcs = pair_src;
   a.n_pairs = n_pairs;
@@ -1593,7 +1662,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
 
 // 32-pair batch wb of a chunk of items [it0, it0 + nit): item it0 + wb / (item_pairs / 32), offset
 // (wb mod (item_pairs / 32)) * 32 in it; its records start at slot 32 wb of the chunk.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
     pair_root_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int it0, int nit,
                            int item_pairs, const BatchRec rec) {
   const int lane = threadIdx.x & 31;
@@ -1652,7 +1721,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
       mine.valid = h[5] != 0.0;
     }
     const unsigned vm = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
-    phase_d_single(a, sm, reinterpret_cast<const float2*>(rec.A + r0 * (L + 1)), L + 1, 1, rec.E + r0 * 33,
+    phase_d_single<ArDW>(a, sm, reinterpret_cast<const float2*>(rec.A + r0 * (L + 1)), L + 1, 1, rec.E + r0 * 33,
                    rec.R2 + r0 * Mt, mine, vm, item.p0 + off, nb);
   }
 }
@@ -1862,6 +1931,7 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
   int64_t off = 0;
   for (int i = 0; i < n_surf; ++i) {
     PairArgs a = make_pair_args(surfs[i], ks[i], kernels);
+    a.fp64_transforms = 0;   // the batch kernels run the single layer in double words
     a.enumerate = 1;
     a.p0 = 0;
     a.n_pairs = (int64_t)16 * surfs[i]->Np * 48 * surfs[i]->Mt;

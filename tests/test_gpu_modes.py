@@ -80,3 +80,21 @@ def test_invalid_pair_reports_error(bie, ctx, ggq):
         ctx.sync()
     assert torch.all(out[0] == 0)
     ctx.sync()  # the status word was cleared
+
+
+def test_fp64_transforms_option(bie, ggq):
+    """The single layer's transforms in FP64 (a context option) against the oracle, per pair and in the
+    assembled rows (FP64 weights and near fill)."""
+    ctx = bie.Context()
+    ctx.set_option(bie.OPT_FP64_TRANSFORMS, 1)
+    _check(bie, ctx, ggq, wl.ellipsoid(1.0, 0.8, 0.6), 16, 128, 10.0, 400, seed=7)
+    _check(bie, ctx, ggq, wl.bumpy(), 6, 96, 5.0, 300, seed=8)
+    from oracle import nystrom as ny
+    s = bie.Surface(ctx, wl.ellipsoid(1.0, 0.8, 0.6), 4, 64, ggq)
+    A = bie.assemble(s, bie.OP_S, 4.0)
+    ctx.sync()
+    rows = np.unique(np.concatenate([wl.sample_rows(4, 64, 10, seed=5), [0, s.N - 1]]))
+    got = A[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ref = ny.operator_rows(wl.ellipsoid(1.0, 0.8, 0.6), 4, 64, 4.0, ggq[0], ggq[1], rows, op="S")
+    err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert err.max() <= TOL, err.max()
