@@ -60,7 +60,13 @@ __device__ __forceinline__ float2 dw_from(double v) {
   }
   const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
   const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-  const float rest = __uint2float_rn((unsigned)(b & 0x1fffffffu));
+  // the 29-bit remainder r as a float, rounded to nearest, with FP32 instructions only (an integer
+  // conversion instruction would run on the FP64 pipe): r = 64 rh + rl with rh < 2^23 and rl < 64 are
+  // exact floats by the 2^23 bias trick, and one FMA rounds 64 rh + rl once
+  const unsigned r = (unsigned)(b & 0x1fffffffu);
+  const float fh = __uint_as_float(0x4B000000u | (r >> 6)) - 8388608.0f;
+  const float fl = __uint_as_float(0x4B000000u | (r & 63u)) - 8388608.0f;
+  const float rest = fmaf(fh, 64.0f, fl);
   const float l = (__uint_as_float(sgn | __float_as_uint(rest)) * 5.421010862427522e-20f)   // * 2^-64
                   * __uint_as_float((unsigned)(e - 884) << 23);                            // * 2^(e - 1011)
   return make_float2(h, l);

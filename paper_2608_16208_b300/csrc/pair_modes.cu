@@ -1219,7 +1219,7 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
 }
 
 template <bool kWithK>
-__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock) pair_kernel(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) pair_kernel(const __grid_constant__ PairArgs a) {
   extern __shared__ double smem[];
   const int wib = threadIdx.x >> 5;
   const size_t per_warp = smem_doubles(a.Mt, a.P, a.L, kWithK);
