@@ -366,7 +366,9 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     sk_ms = e0.elapsed_time(e1)
-    del modes_sk, rows_all, srcs_all, panel, keep
+    del modes_sk
+    banded = run_banded_route(bie, surf, k, rows_all, srcs_all, flush, stream)
+    del rows_all, srcs_all, panel, keep
     fp64_peak = fp64_peak_gflops()
     fl = algorithmic_flops_per_pair(Mt)
     traffic = (PAIR_TRAFFIC["bytes_per_pair"] * pairs
@@ -457,10 +459,36 @@ def run_gpu(args):
             "rows": rows,
             "single_and_double_layer": {"pairs_per_s": pk_pairs / (sk_ms / 1000.0), "ms": sk_ms, "pairs": pk_pairs,
                                         "kernels": "S+K", "path": "fused FP64 pair kernel"},
+            "banded_route": banded,
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_banded_route(bie, surf, k, rows_all, srcs_all, flush, stream, n=75776):
+    """The O(M) route to the single layer (Section 3.3, Eq. (Sphi:appr2) over the banded system
+    Eq. (Axb)) on the first n pairs of the workload: its rate, one launch timed with events after a
+    warm-up, and its normwise difference from the singularity-swapping route on the same pairs."""
+    import torch
+    n = min(n, rows_all.numel())
+    r, c = rows_all[:n].contiguous(), srcs_all[:n].contiguous()
+    out = bie.kernel_modes_banded(surf, k, r, c)
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bie.kernel_modes_banded(surf, k, r, c, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ref = bie.kernel_modes(surf, bie.KERNEL_S, k, r, c)[:, 0]
+    surf.ctx.sync()
+    diff = (out - ref).abs().amax(dim=1) / ref.abs().amax(dim=1)
+    return {"pairs": n, "ms": ms, "pairs_per_s": n / (ms / 1000.0),
+            "vs_swapped_route": {"max_normwise": float(diff.max()), "median_normwise": float(diff.median())},
+            "path": "bie_kernel_modes_banded: <rho^{-1}>_l by the banded system (m0 = 2 on the ellipsoid), "
+                    "boundary modes by graded Gauss-Legendre quadrature, convolution with the grid modes "
+                    "of cos(k rho)"}
 
 
 def accuracy_vs_oracle(c, rows, srcs, got):
@@ -787,9 +815,26 @@ def run_profile_case(name):
         surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
         W = torch.empty((1, 1 << 18, max(sp["Mt"] for sp in specs)), dtype=torch.complex128, device="cuda")
         plan = bie.Batch(ctx, surfs, [sp["k"] for sp in specs], bie.KERNEL_S, W, 1 << 18)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         plan.run()
+        e1.record()
         ctx.sync()
-        print("batch: %d pairs, config %s" % (plan.pairs, plan.config))
+        print("batch: %d pairs, config %s, %.1f ms" % (plan.pairs, plan.config, e0.elapsed_time(e1)))
+    elif name == "banded":        # the O(M) route to the single layer on 18,944 pairs of the workload
+        s = bie.Surface(ctx, c["surface"], c["Np"], c["Mt"], ggq)
+        n = 18944
+        rows = 16 * c["Mt"] * (c["Np"] // 2) + torch.arange(n, device="cuda", dtype=torch.int64) // 48
+        srcs = torch.arange(n, device="cuda", dtype=torch.int32) % 48
+        out = bie.kernel_modes_banded(s, c["k"], rows, srcs)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bie.kernel_modes_banded(s, c["k"], rows, srcs, out=out)
+        e1.record()
+        ctx.sync()
+        print("banded: %d pairs, finite: %s, %.3f ms" % (n, bool(torch.isfinite(torch.view_as_real(out)).all()),
+                                                       e0.elapsed_time(e1)))
     elif name == "precond":       # block-diagonal factors and one training step of the network, N = 24,576
         desc, k, d = learned_family(1, 0)
         s = bie.Surface(ctx, desc, 16, 96, ggq)
@@ -816,7 +861,7 @@ def main():
     ap.add_argument("--batch-surfaces", type=int, default=64, help="surfaces in the batch-scheduler run (0: skip)")
     ap.add_argument("--profile-case", default="",
                     help="profiling aid: one small launch of a kernel family (assemble, products, field, batch, "
-                         "precond) and exit")
+                         "banded, precond) and exit")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: run the pair pipeline once on this many pairs of the workload and exit")
     args = ap.parse_args()

@@ -222,6 +222,43 @@ bie_status bie_kernel_modes_noalloc(bie_ctx ctx, bie_surface s, unsigned kernels
  * form is much better conditioned for iterative solvers.                      */
 #define BIE_UNWEIGHTED 0x100
 
+/* ---- the O(M) route (Section 3.3, "An O(M) approach") ---------------------
+ * bie_rho_inv_modes: for each query q with target x = r(t[q], theta[q]) and
+ * source ring t_s = ts[q] (t != t_s), the theta_s-Fourier modes
+ *   <rho^{-1}>_l = (1/2pi) int_0^{2pi} e^{-i l theta_s} / |r(t_s, theta_s) - x| dtheta_s,
+ * l = 0..lmax (<rho^{-1}>_{-l} is the conjugate), by the difference equation of
+ * Eq. (lin:diff): the modes of rho^2 from 64 samples, m0 by Eq. (crt:M0) (every
+ * mode beyond m0 below eps0 times the largest), the first and last m0 modes by
+ * Gauss-Legendre quadrature on panels graded towards the minimiser of rho^2
+ * (Eq. (offline:terms)), the others from the banded system Eq. (Axb) by
+ * Gaussian elimination with partial pivoting inside the band.
+ *   t, theta, ts [dev] double[n]; modes_out [dev] double2[n][lmax + 1];
+ *   m0_out [dev] int32[n] or NULL: the m0 of each query.
+ *   lmax >= 4d + 1 and <= 65536, where d is the surface's theta-degree (1 for
+ *   the ellipsoid, bean and tori, 1 + max m for a star, max m for a Fourier
+ *   torus); 2d <= 15.  eps0 in (0, 1e-6]; the paper's value is 1e-14; m0 <= 2d.
+ * Accuracy: the route takes rho^2 through its modes, whose rounding (relative
+ * to max rho^2) is amplified near the minimiser by 1/min rho^2: it serves
+ * pairs that are not extremely close (the paper recommends singularity
+ * swapping, bie_kernel_modes, for close pairs unless Mth is very large).
+ * Errors: BIE_EINVAL, BIE_ECUDA; a query with t == t_s, a non-finite input or a
+ * zero pivot gets NaN modes, and the next bie_ctx_sync returns BIE_ENAN.
+ * Not for stream capture (the call may grow its device scratch).              */
+bie_status bie_rho_inv_modes(bie_ctx ctx, bie_surface s, const double* t, const double* theta,
+                             const double* ts, int64_t n, int lmax, double eps0, double* modes_out,
+                             int32_t* m0_out);
+/* bie_kernel_modes_banded: single-layer modes K_m, m = -M..M (M = Mth/2), of
+ * the pairs of bie_kernel_modes (same pair_row / pair_src encoding and output
+ * layout double2[n_pairs][Mth + 1]) through the O(M) route: Eq. (Sphi:appr2)
+ * with M0 = M, K_m = sum_j <cos k rho>_j <rho^{-1}>_{m-j} + i <sin(k rho)/rho>_m,
+ * the grid modes of cos(k rho) and sin(k rho)/rho (j = -M..M, the Nyquist mode
+ * split evenly) from one FFT of length Mth, <rho^{-1}>_l (l <= Mth) as in
+ * bie_rho_inv_modes.  Mth <= 1024 and Mth >= 4d + 1.
+ * Errors: as bie_rho_inv_modes; invalid pairs as bie_kernel_modes.            */
+bie_status bie_kernel_modes_banded(bie_ctx ctx, bie_surface s, double k, const int64_t* pair_row,
+                                   const int32_t* pair_src, int64_t n_pairs, double eps0,
+                                   double* modes_out);
+
 /* ---- batch scheduler -------------------------------------------------------
  * Many surfaces of uneven size (panels, Mth, wavenumber) in a few launches.
  * bie_batch_create builds a device-resident plan: the near pairs of every

@@ -27,6 +27,10 @@ Every smooth factor keeps all Mth of its grid modes (the paper's p and M_0
 set to M), with the Nyquist mode split evenly between +M and -M.
 Convolutions are written as direct sums.
 
+``rho_inv_modes_banded`` and ``method_modes_banded`` follow the paper's other route to the modes
+of 1/rho (Section 3.3, "An O(M) approach"): the difference equation Eq. (lin:diff) solved as the
+banded system Eq. (Axb) with quadrature boundary values, then Eq. (Sphi:appr2) as in step 5.
+
 ``definition_modes`` is the plain definition <f>_m = (1/2pi) int f e^{-im th}
 evaluated by the trapezoid rule on a grid refined until it converges
 (brute force, no singularity swapping).
@@ -433,6 +437,26 @@ def rho_inv_modes_banded(surface, t, th, t_s, lmax, eps0=1e-14):
                 b[i] -= a * out[i + j]
     out[m0:lmax - m0 + 1] = np.linalg.solve(A, b)
     return out, m0
+
+
+def method_modes_banded(surface, t, th, t_s, Mt, k, eps0=1e-14):
+    """Single-layer modes K_m, m = -M..M, through the O(M) route: Eq. (Sphi:appr2) with M_0 = M, the
+    modes of 1/rho for |l| <= 2M from rho_inv_modes_banded (Eq. (lin:diff)), the grid modes of cos(k rho)
+    and of the smooth part i sin(k rho)/rho as in method_modes.  Returns (B, Mt+1) complex."""
+    t = np.atleast_1d(np.asarray(t, float))
+    th = np.atleast_1d(np.asarray(th, float))
+    t_s = np.atleast_1d(np.asarray(t_s, float))
+    M = Mt // 2
+    thq = 2 * np.pi * np.arange(Mt) / Mt
+    out = np.zeros((len(t), Mt + 1), complex)
+    for i in range(len(t)):
+        Y, _ = _near_difference(surface, np.full(Mt, t_s[i]), thq, np.full(Mt, t[i]), np.full(Mt, th[i]))
+        rho = np.sqrt(np.sum(Y * Y, -1))
+        Rp, _ = rho_inv_modes_banded(surface, t[i], th[i], t_s[i], 2 * M, eps0)
+        R = np.concatenate([np.conj(Rp[:0:-1]), Rp])[None, :]                # l = -2M..2M
+        C = sym_modes(np.cos(k * rho), M)[None, :]
+        out[i] = linear_convolution(C, R, 2 * M, M)[0] + sym_modes(1j * np.sin(k * rho) / rho, M)
+    return out
 
 
 def definition_rho_inv(surface, t, th, t_s, M, tol=1e-15, n_max=2 ** 22):

@@ -84,6 +84,8 @@ _sig("bie_surface_normals", _vp, [_vp])
 _sig("bie_surface_jacobians", _vp, [_vp])
 _sig("bie_kernel_modes", _i32, [_vp, _vp, _u, _d, _vp, _vp, _i64, _vp])
 _sig("bie_kernel_modes_noalloc", _i32, [_vp, _vp, _u, _d, _vp, _vp, _i64, _vp])
+_sig("bie_rho_inv_modes", _i32, [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _d, _vp, _vp])
+_sig("bie_kernel_modes_banded", _i32, [_vp, _vp, _d, _vp, _vp, _i64, _d, _vp])
 
 
 class BieError(RuntimeError):
@@ -202,6 +204,28 @@ def kernel_modes(surface, kernels, k, rows, srcs, out=None):
         out = torch.empty((n, nk, surface.Mt + 1), dtype=torch.complex128, device="cuda")
     check(lib.bie_kernel_modes(surface.ctx.h, surface.h, kernels, float(k), _ptr(rows), _ptr(srcs), n,
                                _ptr(out)), "bie_kernel_modes")
+    return out
+
+
+def rho_inv_modes(surface, t, th, ts, lmax, eps0=1e-14):
+    """O(M) route: <rho^{-1}>_l, l = 0..lmax, of the queries (t, th, ts) (float64 CUDA tensors):
+    complex128 tensor [n, lmax+1] and the int32 m0 of each query."""
+    t, th, ts = (torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous() for v in (t, th, ts))
+    n = t.numel()
+    out = torch.empty((n, lmax + 1), dtype=torch.complex128, device="cuda")
+    m0 = torch.zeros(n, dtype=torch.int32, device="cuda")
+    check(lib.bie_rho_inv_modes(surface.ctx.h, surface.h, _ptr(t), _ptr(th), _ptr(ts), n, int(lmax), float(eps0),
+                                _ptr(out), _ptr(m0)), "bie_rho_inv_modes")
+    return out, m0
+
+
+def kernel_modes_banded(surface, k, rows, srcs, eps0=1e-14, out=None):
+    """Single-layer modes K_m, m = -M..M, per pair through the O(M) route: complex128 [n, Mt+1]."""
+    n = rows.numel()
+    if out is None:
+        out = torch.empty((n, surface.Mt + 1), dtype=torch.complex128, device="cuda")
+    check(lib.bie_kernel_modes_banded(surface.ctx.h, surface.h, float(k), _ptr(rows), _ptr(srcs), n, float(eps0),
+                                      _ptr(out)), "bie_kernel_modes_banded")
     return out
 
 

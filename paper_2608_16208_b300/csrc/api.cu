@@ -130,6 +130,7 @@ void bie_ctx_free(bie_ctx ctx) {
   delete ctx->marks;
   cudaFree(ctx->pair_scratch);
   cudaFree(ctx->pair_records);
+  cudaFree(ctx->band_scratch);
   cudaFree(ctx->d_status);
   delete ctx;
 }
@@ -150,6 +151,11 @@ bie_status bie_ctx_sync(bie_ctx ctx) {
     bie::set_error("a bounded device wait expired (tensor-core product)");
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
     return BIE_ETIMEOUT;
+  }
+  if (st[2]) {
+    bie::set_error("O(M) route: %d queries with t == t_s, a non-finite input or a singular banded system", st[2]);
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
+    return BIE_ENAN;
   }
   return BIE_OK;
 }

@@ -211,11 +211,12 @@ static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double t
     return;
   }
   double h = 1.0, ht = 0.0, hth = 0.0, htt = 0.0, htth = 0.0, hthth = 0.0;
+  double sm = 0.0, cm = 1.0;
   for (int i = 0; i < S.nt; ++i) {
-    double gg, gt, gtt, sm, cm;
+    double gg, gt, gtt;
     scpow_d(st, ct, S.p[i], S.q[i], &gg, &gt, &gtt);
     const double mm = S.m[i];
-    sincos(mm * th, &sm, &cm);
+    if (i == 0 || S.m[i] != S.m[i - 1]) sincos(mm * th, &sm, &cm);   // reused along a run of equal m
     double T, Tth, Tthth;
     if (S.s[i] == 0) {
       T = cm; Tth = -mm * sm; Tthth = -mm * mm * cm;
@@ -302,12 +303,12 @@ static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx t
     return;
   }
   cplx h = C(1.0), ht = C(0.0), hth = C(0.0);
+  cplx cm = C(1.0), sm = C(0.0);
   for (int i = 0; i < S.nt; ++i) {
     double gg, gt, gtt;
     scpow_d(st, ct, S.p[i], S.q[i], &gg, &gt, &gtt);
     const double mm = S.m[i];
-    cplx cm, sm;
-    ccossin(mm * th, &cm, &sm);
+    if (i == 0 || S.m[i] != S.m[i - 1]) ccossin(mm * th, &cm, &sm);   // reused along a run of equal m
     cplx T, Tth;
     if (S.s[i] == 0) {
       T = cm; Tth = -mm * sm;
@@ -461,6 +462,9 @@ struct bie_ctx_s {
   size_t pair_scratch_bytes = 0;
   double* pair_records = nullptr;
   size_t pair_records_bytes = 0;
+  // the O(M) route's per-warp rows of U (grown on demand)
+  void* band_scratch = nullptr;
+  size_t band_scratch_bytes = 0;
 };
 
 struct bie_surface_s {

@@ -21,7 +21,8 @@ def declared_functions():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for required in ("bie_surface_sample", "bie_kernel_modes", "bie_assemble", "bie_solve", "bie_field_eval",
-                     "bie_blockdiag_create", "bie_net_train", "bie_batch_run", "bie_kernel_modes_noalloc"):
+                     "bie_blockdiag_create", "bie_net_train", "bie_batch_run", "bie_kernel_modes_noalloc",
+                     "bie_rho_inv_modes", "bie_kernel_modes_banded"):
         assert required in names
     assert len(names) >= 38
 
@@ -60,6 +61,8 @@ def test_invalid_arguments_are_refused_before_any_device_call():
         "bie_matrix_create": (null, i64(4), null, u(0), null),
         "bie_matrix_matvec": (null, i32(0), null, i32(1), null),
         "bie_solve_matrix": (null, null, null, i32(1), null, null, null),
+        "bie_rho_inv_modes": (null, null, null, null, null, i64(1), i32(64), d(1e-14), null, null),
+        "bie_kernel_modes_banded": (null, null, d(1.0), null, null, i64(1), d(1e-14), null),
     }
     for name, args in calls.items():
         fn = getattr(lib, name)
