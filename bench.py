@@ -627,13 +627,45 @@ def run_batch(bie, ctx, count, stream):
         ms_seq += e0.elapsed_time(e1)
         del sp
     mts = [sp["Mt"] for sp in specs]
+    del surfs
     return {"surfaces": count, "pairs": plan_pairs, "pairs_per_s": job_rate, "ms": job_ms,
-            "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms, "autotuned": plan_config,
+            "sequential_ms": ms_seq, "sequential_pairs_per_s": plan_pairs / (ms_seq / 1000.0),
+            "speedup_vs_sequential": ms_seq / ms,
+            "single_surface_star": star_single_surface_rate(bie, ctx, ggq, stream), "autotuned": plan_config,
             "m_theta_counts": {str(m): mts.count(m) for m in sorted(set(mts))},
             "panels_range": [min(sp["Np"] for sp in specs), max(sp["Np"] for sp in specs)],
             "rhs_per_surface": [sp["nrhs"] for sp in specs],
             "output": "ring of %d pairs x %d angles (throughput mode)" % (slot, maxMt), "cuda_graph": True,
             "not_measured": "GGQ fill of the weights and the per-surface right-hand sides"}
+
+
+def star_single_surface_rate(bie, ctx, ggq, stream):
+    """The batch family's per-pair cost on the single-surface path at the bench workload's sizes: one
+    harmonic star (eps = 0.15), Np = 16, Mth = 128, k = 10, every near pair through one kernel-modes
+    launch (S), timed with events after a warm-up; the ellipsoid of the headline takes the same
+    launch."""
+    import torch
+    Np, Mt, k = 16, 128, 10.0
+    s = bie.Surface(ctx, wl.harmonic_star(0, 7, 0.15), Np, Mt, ggq)
+    N = s.N
+    rows = torch.arange(N, device="cuda", dtype=torch.int64).repeat_interleave(48)
+    srcs = torch.arange(48, device="cuda", dtype=torch.int32).repeat(N)
+    panel = rows // (16 * Mt) + srcs.to(torch.int64) // 16 - 1
+    keep = (panel >= 0) & (panel < Np)
+    rows, srcs = rows[keep].contiguous(), srcs[keep].contiguous()
+    out = torch.empty((rows.numel(), 1, Mt + 1), dtype=torch.complex128, device="cuda")
+    with torch.cuda.stream(stream):
+        bie.kernel_modes(s, bie.KERNEL_S, k, rows, srcs, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bie.kernel_modes(s, bie.KERNEL_S, k, rows, srcs, out=out)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = rows.numel()
+    del out, rows, srcs, s
+    return {"surface": "harmonic star (35 terms), Np 16, Mth 128, k 10", "pairs": n, "ms": ms,
+            "pairs_per_s": n / (ms / 1000.0)}
 
 
 def learned_family(seed, i):

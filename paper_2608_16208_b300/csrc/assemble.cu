@@ -198,7 +198,9 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
   int group = (int)(((size_t)4 << 30) / per_panel_bytes);
   if (group < 1) group = 1;
   if (group > s->Np) group = s->Np;
-  if (host_band && group > (s->Np + 3) / 4) group = (s->Np + 3) / 4;   // >= 4 groups: copies overlap compute
+  // >= 8 groups: every copy but the last overlaps the next group's pair kernels, and the last one
+  // (the exposed part of the copy) is an eighth of the band
+  if (host_band && group > (s->Np + 7) / 8) group = (s->Np + 7) / 8;
   const int64_t chunk_pairs = panel_pairs * group;
   const cudaStream_t st0 = ctx->stream;
   cplx* W = nullptr;

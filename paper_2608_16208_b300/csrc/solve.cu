@@ -77,49 +77,84 @@ __global__ void __launch_bounds__(256) zgemm64_block_kernel(int64_t n, int nr, c
   }
 }
 
-// FP32 storage: products in FP32, summed in FP32 over 16 loads (32 complex terms) per lane, the
-// chunk sums accumulated in FP64.  The right-hand sides are converted to FP32 by the caller.
+// FP32 storage.  A CTA of 8 warps takes 8 rows (one per warp) and walks the columns in chunks of
+// kCh32 whose right-hand-side values it stages in shared memory once for all 8 rows (the block of
+// right-hand sides is otherwise re-read from L2 for every row: NR times the row's own bytes).  Each
+// lane sums its products in FP32 over 64 columns (8 chunks) and accumulates those sums in FP64.  The
+// right-hand sides are converted to FP32 by the caller.
+constexpr int kCh32 = 256;
 template <int NR>
 __global__ void __launch_bounds__(256) cgemm32_block_kernel(int64_t n, int nr, const float2* __restrict__ A,
                                                             const float2* __restrict__ X, int64_t ldx,
                                                             double2* __restrict__ Y, int64_t ldy) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = w; row < n; row += nw) {
-    const float2* a = A + row * n;
+  __shared__ float2 xs[NR][kCh32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t g = blockIdx.x; g * 8 < n; g += gridDim.x) {
+    const int64_t row = g * 8 + wid;
+    const bool live = row < n;
+    const float2* a = A + (live ? row : 0) * n;
     double dre[NR], dim[NR];
+    float cr[NR], ci[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) dre[j] = dim[j] = 0.0;
-    for (int64_t c0 = lane; c0 < n; c0 += 32 * 32) {
-      float cr[NR], ci[NR];
+    for (int j = 0; j < NR; ++j) {
+      dre[j] = dim[j] = 0.0;
+      cr[j] = ci[j] = 0.f;
+    }
+    int pending = 0;
+    // the row's values of a chunk are loaded one chunk ahead (they do not wait for the staging)
+    constexpr int U = kCh32 / 32;
+    float2 av[U];
 #pragma unroll
-      for (int j = 0; j < NR; ++j) cr[j] = ci[j] = 0.f;
-      for (int u = 0; u < 32; ++u) {
-        const int64_t c = c0 + 32 * u;
-        if (c < n) {
-          const float2 av = __ldcs(a + c);
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = lane + 32 * u;
+      av[u] = (live && c < n) ? __ldcs(a + c) : make_float2(0.f, 0.f);
+    }
+    for (int64_t c0 = 0; c0 < n; c0 += kCh32) {
+      __syncthreads();   // every warp is done with the previous chunk
+      for (int e = threadIdx.x; e < nr * kCh32; e += 256) {
+        const int j = e / kCh32, cc = e % kCh32;
+        const int64_t c = c0 + cc;
+        xs[j][cc] = c < n ? __ldg(X + j * ldx + c) : make_float2(0.f, 0.f);
+      }
+      float2 an[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = c0 + kCh32 + lane + 32 * u;
+        an[u] = (live && c < n) ? __ldcs(a + c) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      if (live) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
             if (j < nr) {
-              const float2 xv = __ldg(X + j * ldx + c);
-              cr[j] = fmaf(av.x, xv.x, fmaf(-av.y, xv.y, cr[j]));
-              ci[j] = fmaf(av.x, xv.y, fmaf(av.y, xv.x, ci[j]));
+              const float2 xv = xs[j][lane + 32 * u];
+              cr[j] = fmaf(av[u].x, xv.x, fmaf(-av[u].y, xv.y, cr[j]));
+              ci[j] = fmaf(av[u].x, xv.y, fmaf(av[u].y, xv.x, ci[j]));
             }
           }
         }
+        if (++pending == 8 || c0 + kCh32 >= n) {
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            dre[j] += cr[j];
+            dim[j] += ci[j];
+            cr[j] = ci[j] = 0.f;
+          }
+          pending = 0;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) av[u] = an[u];
+    }
+    if (live) {
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        dre[j] += cr[j];
-        dim[j] += ci[j];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      if (j < nr) {
-        const double r = warp_sum_d(dre[j]), i = warp_sum_d(dim[j]);
-        if (lane == 0) Y[j * ldy + row] = make_double2(r, i);
+        if (j < nr) {
+          const double r = warp_sum_d(dre[j]), i = warp_sum_d(dim[j]);
+          if (lane == 0) Y[j * ldy + row] = make_double2(r, i);
+        }
       }
     }
   }
