@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(256) cgemm32_block_kernel(int64_t n, int nr, c
         if (++pending == 8 || c0 + kCh32 >= n) {
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
-            dre[j] += cr[j];
-            dim[j] += ci[j];
-            cr[j] = ci[j] = 0.f;
+            if (j < nr) {
+              dre[j] += cr[j];
+              dim[j] += ci[j];
+              cr[j] = ci[j] = 0.f;
+            }
           }
           pending = 0;
         }
@@ -183,37 +185,70 @@ __device__ __forceinline__ double dw_acc_warp_sum(DwAcc s) {
   return warp_sum_d(f2d_bits(s.h) + f2d_bits(s.l));
 }
 
+// A CTA of 8 warps takes 8 rows (one per warp) and walks the columns in chunks of kChDw whose
+// right-hand-side double words it stages in shared memory once for all 8 rows; each row's next chunk
+// is loaded before the staging barrier.
+constexpr int kChDw = 128;
 template <int NR>
 __global__ void __launch_bounds__(256) zgemm_dw_block_kernel(int64_t n, int nr, const double2* __restrict__ A,
                                                              const float4* __restrict__ X, int64_t ldx,
                                                              double2* __restrict__ Y, int64_t ldy) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = w; row < n; row += nw) {
-    const double2* a = A + row * n;
+  __shared__ float4 xs[NR][kChDw];
+  constexpr int U = kChDw / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t g = blockIdx.x; g * 8 < n; g += gridDim.x) {
+    const int64_t row = g * 8 + wid;
+    const bool live = row < n;
+    const double2* a = A + (live ? row : 0) * n;
     DwAcc re[NR], im[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) re[j] = im[j] = DwAcc{0.f, 0.f};
-    for (int64_t c = lane; c < n; c += 32) {
-      const double2 av = __ldcs(a + c);
-      const float2 ar = dw_from(av.x), ai = dw_from(av.y);
+    double2 av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = lane + 32 * u;
+      av[u] = (live && c < n) ? __ldcs(a + c) : make_double2(0.0, 0.0);
+    }
+    for (int64_t c0 = 0; c0 < n; c0 += kChDw) {
+      __syncthreads();   // every warp is done with the previous chunk
+      for (int e = threadIdx.x; e < nr * kChDw; e += 256) {
+        const int j = e / kChDw, cc = e % kChDw;
+        const int64_t c = c0 + cc;
+        xs[j][cc] = c < n ? __ldg(X + j * ldx + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      double2 an[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t c = c0 + kChDw + lane + 32 * u;
+        an[u] = (live && c < n) ? __ldcs(a + c) : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      if (live) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const float2 ar = dw_from(av[u].x), ai = dw_from(av[u].y);
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            if (j < nr) {
+              const float4 xv = xs[j][lane + 32 * u];   // (re.h, re.l, im.h, im.l)
+              dw_madd(re[j], ar.x, ar.y, xv.x, xv.y);
+              dw_madd(re[j], -ai.x, -ai.y, xv.z, xv.w);
+              dw_madd(im[j], ar.x, ar.y, xv.z, xv.w);
+              dw_madd(im[j], ai.x, ai.y, xv.x, xv.y);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) av[u] = an[u];
+    }
+    if (live) {
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
         if (j < nr) {
-          const float4 xv = __ldg(X + j * ldx + c);   // (re.h, re.l, im.h, im.l)
-          dw_madd(re[j], ar.x, ar.y, xv.x, xv.y);
-          dw_madd(re[j], -ai.x, -ai.y, xv.z, xv.w);
-          dw_madd(im[j], ar.x, ar.y, xv.z, xv.w);
-          dw_madd(im[j], ai.x, ai.y, xv.x, xv.y);
+          const double r = dw_acc_warp_sum(re[j]), i = dw_acc_warp_sum(im[j]);
+          if (lane == 0) Y[j * ldy + row] = make_double2(r, i);
         }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      if (j < nr) {
-        const double r = dw_acc_warp_sum(re[j]), i = dw_acc_warp_sum(im[j]);
-        if (lane == 0) Y[j * ldy + row] = make_double2(r, i);
       }
     }
   }
