@@ -278,6 +278,8 @@ bie_status bie_kernel_modes_banded(bie_ctx ctx, bie_surface s, double k, const i
  * CUDA graph (call it once before capture).  At most 64 distinct Mth per plan.
  * Output: the Parseval weights of pair p of surface i (its enumerated index)
  * go to row (bie_batch_offset(plan, i) + p) % slot_pairs of weights_out [dev]
+ * (the offsets follow the processing order: classes by decreasing Mth,
+ * surfaces in their order within a class)
  * double2[nk][slot_pairs][max Mth] (row length = largest Mth of the batch;
  * kernel blocks in bit order).  slot_pairs >= bie_batch_pairs(plan) keeps
  * every row; smaller values make a bounded ring (throughput runs).
@@ -286,6 +288,20 @@ bie_status bie_kernel_modes_banded(bie_ctx ctx, bie_surface s, double k, const i
 bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surface* surfs, const double* ks,
                             unsigned kernels, double* weights_out, int64_t slot_pairs, bie_batch* out);
 bie_status bie_batch_run(bie_batch plan);
+/* bie_batch_set_fill: throughput mode with the GGQ fill (Section 3.4, Eq. (S123)):
+ * once every pair of a target panel has its Parseval weights, bie_batch_run
+ * folds them with the panel's GGQ / Lagrange coefficients into that panel's
+ * near band, as bie_assemble_near_band does for one surface (single layer,
+ * weighted density, S scaled by h/2; rows [16 Mth][3][16 Mth], slots of source
+ * panels outside the surface zeroed).  Panel f of the run (in processing order)
+ * goes to slot f % band_slots of band_ring [dev] double2[band_slots][16 maxMth]
+ * [3][16 maxMth] (a bounded per-wave buffer: slots are overwritten), with row
+ * length 3*16*Mth of its own surface.  Single-layer plans only.  The ring of
+ * weight rows must hold one panel plus one chunk of the plan: the chunk is cut
+ * to fit.  band_ring = NULL turns the fill off.
+ * Errors: BIE_EINVAL (slot_pairs below a panel plus one item), BIE_EUNSUPPORTED
+ * (a plan with a double layer).                                             */
+bie_status bie_batch_set_fill(bie_batch plan, double* band_ring, int band_slots);
 int64_t bie_batch_pairs(bie_batch plan);
 int64_t bie_batch_offset(bie_batch plan, int i);
 void bie_batch_config(bie_batch plan, int* item_pairs, int* warps_per_block, int* blocks);

@@ -478,6 +478,7 @@ _sig("bie_batch_offset", _i64, [_vp, _i32])
 _sig("bie_batch_config", None, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)])
 _sig("bie_batch_free", None, [_vp])
 _sig("bie_batch_launches", _i32, [_vp])
+_sig("bie_batch_set_fill", _i32, [_vp, _vp, _i32])
 _sig("bie_shard_surfaces", _i32, [_i32, _vp, _i32, _vp, _vp])
 
 
@@ -505,6 +506,16 @@ class Batch:
                                    ctypes.byref(self.h)), "bie_batch_create")
         self.pairs = lib.bie_batch_pairs(self.h)
         self.offsets = [lib.bie_batch_offset(self.h, i) for i in range(len(surfaces))]
+        a, b, c = _i32(), _i32(), _i32()
+        lib.bie_batch_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        self.config = {"item_pairs": a.value, "warps_per_block": b.value, "blocks": c.value,
+                       "launches": lib.bie_batch_launches(self.h)}
+
+    def set_fill(self, band, slots):
+        """GGQ fill into a ring of `slots` near-band slots (band: complex128 [slots, 16 maxMt, 3, 16 maxMt]),
+        or off with band=None."""
+        self.band = band
+        check(lib.bie_batch_set_fill(self.h, None if band is None else _ptr(band), int(slots)), "bie_batch_set_fill")
         a, b, c = _i32(), _i32(), _i32()
         lib.bie_batch_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
         self.config = {"item_pairs": a.value, "warps_per_block": b.value, "blocks": c.value,

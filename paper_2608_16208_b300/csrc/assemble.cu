@@ -174,6 +174,48 @@ __global__ void near_fill_kernel(int Np, int Mt, int periodic, int jpanel, cplx 
   }
 }
 
+// Near fill of one target panel into its near band from Parseval weights kept in a ring of pair
+// rows (the batch scheduler's throughput mode): the weights of pair pp of the panel (pp in the
+// panel's enumeration order) at ring row (pbase + pp) % ring, row length w_ld.  Single layer,
+// weighted density; band [16 Mt rows][3][16 Mt], entries overwritten, slots of source panels outside
+// the surface zeroed.  Block per (local target node, delta), as near_fill_kernel.
+__global__ void near_fill_ring_kernel(int Np, int Mt, int periodic, int jpanel, cplx sS,
+                                      const double* __restrict__ coef, const cplx* __restrict__ W, int64_t pbase,
+                                      int64_t ring, int w_ld, cplx* __restrict__ band) {
+  const int tl = blockIdx.x;            // l * Mt + i
+  const int d = blockIdx.y;
+  const int l = tl / Mt, i = tl % Mt;
+  int ip = jpanel + d - 1;
+  if (periodic) ip = (ip + Np) % Np;
+  cplx* Arow = band + (int64_t)tl * 3 * 16 * Mt + (int64_t)d * 16 * Mt;
+  if (ip < 0 || ip >= Np) {
+    for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) Arow[e] = C(0.0);
+    return;
+  }
+  const int64_t pp0 = (((int64_t)l * 3 + d) * 16) * Mt + i;   // pair (l, d, g = 0, i) of the panel
+  const double* cf = coef + ((d * 16 + l) * 16) * 16;          // [g][n]
+  for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
+    const int n = e / Mt, lp = e % Mt;
+    cplx acc = C(0.0);
+#pragma unroll 4
+    for (int g = 0; g < 16; ++g) {
+      const int64_t r = (pbase + pp0 + (int64_t)g * Mt) % ring;
+      acc = acc + cf[g * 16 + n] * W[r * w_ld + lp];
+    }
+    Arow[e] = sS * acc;
+  }
+}
+
+bie_status near_fill_ring(bie_surface s, int jpanel, const cplx* W, int64_t pbase, int64_t ring, int w_ld,
+                          cplx* band, cudaStream_t st) {
+  const int Mt = s->Mt;
+  const cplx sS = C(0.5 * s->h);
+  near_fill_ring_kernel<<<dim3(16 * Mt, 3), 256, 0, st>>>(s->Np, Mt, s->sp.periodic, jpanel, sS, s->near_coef, W, pbase,
+                                                          ring, w_ld, band);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BIE_OK : cuda_fail(e, "near_fill_ring_kernel");
+}
+
 }  // namespace bie
 
 using namespace bie;

@@ -502,6 +502,9 @@ void set_error(const char* fmt, ...);
 bie_status cuda_fail(cudaError_t e, const char* where);
 // BIE_OK if the context's device is the current one, else BIE_EINVAL naming the call
 bie_status check_device(bie_ctx ctx, const char* where);
+// near fill of one target panel of s into a band buffer from weights in a ring of pair rows
+bie_status near_fill_ring(bie_surface s, int jpanel, const bie::cplx* W, int64_t pbase, int64_t ring, int w_ld,
+                          bie::cplx* band, cudaStream_t st);
 // preconditioners (blockdiag.cu, precond_net.cu)
 bie_status blockdiag_apply_dev(bie_blockdiag P, const double2* r, int nv, double2* z);
 bie_status blockdiag_apply_f32(bie_blockdiag P, const float2* r, int nv, float2* z);

@@ -1646,6 +1646,15 @@ struct bie_batch_s {
   double* scratch = nullptr;    // fused path: per resident warp recurrence scratch
   double* records = nullptr;    // split path: per-pair records of one chunk
   float tuned_ms = 0.f;
+  std::vector<bie_surface> surfs;
+  std::vector<bie::BatchItem> h_items;   // split path: the work list, as uploaded
+  int64_t slot_pairs = 0;
+  // GGQ fill (single layer): each target panel, once its pairs are done, folded into a ring of
+  // band_slots near-band slots of band_slot_elems complex each
+  bie::cplx* band = nullptr;
+  int band_slots = 0;
+  int64_t band_slot_elems = 0;
+  bool fill_on() const { return band != nullptr; }
 };
 
 namespace bie {
@@ -1761,6 +1770,11 @@ static bie_status batch_launch(bie_batch_s& b, int it_hi) {
                                                                        b.d_counter + ci, b.scratch, b.scratch_per_warp, c.Mt);
     }
   } else {
+    // GGQ fill bookkeeping: pairs done per surface (its items are contiguous and in order), panels
+    // already folded, and the next band slot
+    std::vector<int64_t> done(b.fill_on() ? b.n_surf : 0, 0);
+    std::vector<int> filled(done.size(), 0);
+    int64_t slot = 0;
     for (const BatchClass& c : b.classes) {
       const int end = std::min(c.it_end, it_hi);
       if (end <= c.it_begin) break;
@@ -1773,6 +1787,22 @@ static bie_status batch_launch(bie_batch_s& b, int it_hi) {
         const int bt = (int)std::max<int64_t>(1, std::min<int64_t>(c.tr_blocks, (wbs + c.tr_wpb - 1) / c.tr_wpb));
         pair_transform_batch_kernel<<<bt, 32 * c.tr_wpb, c.tr_smem, st>>>(b.d_args, b.d_items, i0, nit, b.item_pairs,
                                                                          rec);
+        if (!b.fill_on()) continue;
+        for (int it = i0; it < i0 + nit; ++it) {
+          const BatchItem& item = b.h_items[it];
+          done[item.surf] = item.p0 + item.n;
+        }
+        for (int sidx = 0; sidx < b.n_surf; ++sidx) {
+          const bie_surface sf = b.surfs[sidx];
+          const int64_t panel_pairs = (int64_t)16 * 48 * sf->Mt;
+          for (; filled[sidx] < sf->Np && (int64_t)(filled[sidx] + 1) * panel_pairs <= done[sidx]; ++filled[sidx]) {
+            const bie_status fs = near_fill_ring(sf, filled[sidx], reinterpret_cast<const cplx*>(b.host_args[sidx].weights_out),
+                                                 b.offsets[sidx] + (int64_t)filled[sidx] * panel_pairs, b.slot_pairs,
+                                                 b.maxMt, b.band + (slot % b.band_slots) * b.band_slot_elems, st);
+            if (fs != BIE_OK) return fs;
+            ++slot;
+          }
+        }
       }
     }
   }
@@ -1819,6 +1849,21 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     set_error("bie_batch_create: more than %d grid sizes", kMaxBatchClasses);
     return BIE_EUNSUPPORTED;
   }
+  // output rows follow the processing order (classes by decreasing Mth, surfaces in order within a
+  // class), so that a bounded ring holds the most recent pairs of every surface
+  std::vector<int> order(n_surf);
+  for (int i = 0; i < n_surf; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return surfs[x]->Mt > surfs[y]->Mt; });
+  std::vector<int64_t> start(n_surf, 0);
+  {
+    int64_t acc = 0;
+    for (int i : order) {
+      start[i] = acc;
+      acc += (int64_t)16 * surfs[i]->Np * 48 * surfs[i]->Mt;
+    }
+  }
+  b->slot_pairs = slot_pairs;
+  b->surfs.assign(surfs, surfs + n_surf);
   int64_t off = 0;
   for (int i = 0; i < n_surf; ++i) {
     PairArgs a = make_pair_args(surfs[i], ks[i], kernels);
@@ -1828,10 +1873,10 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     a.n_pairs = (int64_t)16 * surfs[i]->Np * 48 * surfs[i]->Mt;
     a.weights_out = (cplx*)weights_out;
     a.w_ld = b->maxMt;
-    a.out_base = off;
+    a.out_base = start[i];
     a.out_mod = slot_pairs;
     a.weights_stride = slot_pairs * b->maxMt;
-    b->offsets.push_back(off);
+    b->offsets.push_back(start[i]);
     off += a.n_pairs;
     b->host_args.push_back(a);
   }
@@ -1869,6 +1914,7 @@ extern "C" bie_status bie_batch_create(bie_ctx ctx, int n_surf, const bie_surfac
     const std::vector<BatchItem> items = make_items(*b, b->item_pairs);
     b->n_items = (int)items.size();
     b->classes = make_classes(*b, items);
+    b->h_items = items;
     st = upload_items(*b, items);
     for (auto& c : b->classes)
       if (st == BIE_OK && !configure_class(*b, c)) { st = BIE_EUNSUPPORTED; set_error("bie_batch_create: a class does not fit"); }
@@ -1950,7 +1996,37 @@ extern "C" int bie_batch_launches(bie_batch b) {
   if (!b->split) return (int)b->classes.size();
   int n = 0;
   for (const BatchClass& c : b->classes) n += 2 * ((c.it_end - c.it_begin + b->chunk_items - 1) / b->chunk_items);
+  if (b->fill_on())
+    for (const bie_surface sf : b->surfs) n += sf->Np;   // one GGQ fill per target panel
   return n;
+}
+
+extern "C" bie_status bie_batch_set_fill(bie_batch b, double* band_ring, int band_slots) {
+  if (!b || (band_ring && band_slots < 1)) { set_error("bie_batch_set_fill: invalid arguments"); return BIE_EINVAL; }
+  if (!band_ring) {
+    b->band = nullptr;
+    b->band_slots = 0;
+    return BIE_OK;
+  }
+  if (!b->split) {
+    set_error("bie_batch_set_fill: the GGQ fill takes single-layer plans (kernels = BIE_KERNEL_S)");
+    return BIE_EUNSUPPORTED;
+  }
+  int64_t max_panel = 0;
+  for (const bie_surface sf : b->surfs) max_panel = std::max<int64_t>(max_panel, (int64_t)16 * 48 * sf->Mt);
+  // a panel straddling two chunks keeps its first rows while the next chunk runs: the ring holds a
+  // chunk plus a panel
+  const int64_t room = (b->slot_pairs - max_panel) / b->item_pairs;
+  if (room < 1) {
+    set_error("bie_batch_set_fill: slot_pairs %lld holds less than a panel (%lld pairs) plus one item",
+              (long long)b->slot_pairs, (long long)max_panel);
+    return BIE_EINVAL;
+  }
+  if (b->chunk_items > room) b->chunk_items = (int)room;
+  b->band = reinterpret_cast<bie::cplx*>(band_ring);
+  b->band_slots = band_slots;
+  b->band_slot_elems = (int64_t)16 * b->maxMt * 3 * 16 * b->maxMt;
+  return BIE_OK;
 }
 
 extern "C" void bie_batch_free(bie_batch b) {
