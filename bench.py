@@ -849,11 +849,14 @@ def run_profile_case(name):
         bie.field_eval(s, bie.OP_S, c["k"], dens, wl.exterior_points(1024, 3.0))
         ctx.sync()
         print("field: %d sources x 1024 points" % s.N)
-    elif name == "batch":         # the split batch path: four harmonic stars, Mth 64..256
+    elif name == "batch":         # the split batch path with the GGQ fill: four harmonic stars, Mth 64..256
         specs = wl.batch_surfaces(seed=0, count=4)
         surfs = [bie.Surface(ctx, sp["surface"], sp["Np"], sp["Mt"], ggq) for sp in specs]
-        W = torch.empty((1, 1 << 18, max(sp["Mt"] for sp in specs)), dtype=torch.complex128, device="cuda")
-        plan = bie.Batch(ctx, surfs, [sp["k"] for sp in specs], bie.KERNEL_S, W, 1 << 18)
+        W = torch.empty((1, 1 << 20, max(sp["Mt"] for sp in specs)), dtype=torch.complex128, device="cuda")
+        plan = bie.Batch(ctx, surfs, [sp["k"] for sp in specs], bie.KERNEL_S, W, 1 << 20)
+        maxMt = max(sp["Mt"] for sp in specs)
+        band = torch.empty((2, 16 * maxMt, 3, 16 * maxMt), dtype=torch.complex128, device="cuda")
+        plan.set_fill(band, 2)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         plan.run()
