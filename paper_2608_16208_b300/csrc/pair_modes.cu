@@ -102,13 +102,15 @@ __device__ __forceinline__ PairInfo bcast(const PairInfo& p, int src) {
   return o;
 }
 
-__device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, cplx z, cplx* f, cplx* df) {
+// tb: the pair's star table (stars with at most kStarTabTerms terms), or null
+__device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, const StarTab* tb, cplx z, cplx* f, cplx* df) {
   C3 r, rt, rth;
-  surf_eval_c(S, P.ts, z, &r, &rt, &rth);
+  if (tb) surf_eval_c_star_tab(S, *tb, z, &r, &rt, &rth);
+  else surf_eval_c(S, P.ts, z, &r, &rt, &rth);
   C3 Y = {r.x - C(P.x), r.y - C(P.y), r.z - C(P.z)};
   const bool near = fabs(P.ts - P.t) + fabs(wrap_pi(z.re - P.th)) <= kStableDelta ||
                     abs2(Y.x) + abs2(Y.y) + abs2(Y.z) <= kStableDist * kStableDist;
-  if (near) Y = diff_ana<cplx>(S, P.ts, z, P.t, P.th);
+  if (near) Y = tb ? diff_star_tab<cplx>(S, *tb, z, P.th) : diff_ana<cplx>(S, P.ts, z, P.t, P.th);
   *f = Y.x * Y.x + Y.y * Y.y + Y.z * Y.z;
   *df = 2.0 * (Y.x * rth.x + Y.y * rth.y + Y.z * rth.z);
 }
@@ -118,9 +120,16 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
   double a0 = kTwoPi * P.bi / Mt;   // same value as the theta table entry
   const double start = a0;
   double g0 = 0, g1 = 0, g2 = 0;
+  StarTab tbs;   // in local memory
+  const StarTab* tb = nullptr;
+  if (S.kind == 1 && S.nt <= kStarTabTerms) {
+    star_tab_fill(S, P.ts, P.t, P.th, &tbs);
+    tb = &tbs;
+  }
   auto eval_r = [&](double z) {
     Geo G;
-    surf_eval(S, P.ts, z, 2, &G);
+    if (tb) surf_eval_star_tab(S, *tb, z, 2, &G);
+    else surf_eval(S, P.ts, z, 2, &G);
     const double yx = G.r.x - P.x, yy = G.r.y - P.y, yz = G.r.z - P.z;
     g0 = yx * yx + yy * yy + yz * yz;
     g1 = 2 * (yx * G.rth.x + yy * G.rth.y + yz * G.rth.z);
@@ -136,7 +145,7 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
   eval_r(a0);
   if (fabs(P.ts - P.t) + fabs(wrap_pi(a0 - P.th)) <= kStableDelta || g0 <= kStableDist * kStableDist) {
     // rho^2(a0) without cancellation
-    const R3 Y = diff_ana<double>(S, P.ts, a0, P.t, P.th);
+    const R3 Y = tb ? diff_star_tab<double>(S, *tb, a0, P.th) : diff_ana<double>(S, P.ts, a0, P.t, P.th);
     g0 = dot(Y, Y);
   }
   const double b0 = sqrt(2 * g0 / (g2 > 0 ? g2 : 0.0));
@@ -146,7 +155,7 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
   bool done = P.capped, extra = false;
   for (int it = 0; it < 60 && !done; ++it) {
     cplx f, df;
-    rho2_cplx(S, P, z, &f, &df);
+    rho2_cplx(S, P, tb, z, &f, &df);
     const cplx dz = cdiv(f, df);
     cplx zn = z - dz;
     if (zn.im < 0) zn = conj(zn);
