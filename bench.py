@@ -703,8 +703,9 @@ def learned_family(seed, i):
 
 def run_learned(bie, n_train=4, n_test=2, steps=600):
     """Learned preconditioner: train on systems of the family, then time FGMRES to 1e-8 on held-out
-    systems with the block-diagonal preconditioner (the judge and fallback) and with the network on
-    top of it.  Operator: the single layer S (first kind, weighted density), plane-wave data."""
+    systems with the block-diagonal preconditioner (the one the network must beat, and its fallback)
+    and with the network on top of it.  Operator: the single layer S (first kind, weighted density),
+    plane-wave data."""
     import torch
     ctx = bie.Context()
     ggq = wl.load_ggq()

@@ -241,7 +241,8 @@ static bie_status near_stage(bie_ctx ctx, bie_surface s, unsigned kernels, doubl
   if (group < 1) group = 1;
   if (group > s->Np) group = s->Np;
   // >= 8 groups: every copy but the last overlaps the next group's pair kernels, and the last one
-  // (the exposed part of the copy) is an eighth of the band
+  // (the exposed part of the copy) is an eighth of the band (16 groups of one panel were slower:
+  // launches of 98,304 pairs leave the root kernel's last wave mostly empty)
   if (host_band && group > (s->Np + 7) / 8) group = (s->Np + 7) / 8;
   const int64_t chunk_pairs = panel_pairs * group;
   const cudaStream_t st0 = ctx->stream;

@@ -66,3 +66,22 @@ def test_fill_refuses_a_ring_without_room(bie, ggq):
     band = torch.zeros((1, 16 * Mt, 3, 16 * Mt), dtype=torch.complex128, device="cuda")
     with pytest.raises(RuntimeError):
         plan.set_fill(band, 1)
+
+
+def test_fill_takes_single_layer_plans_only_and_turns_off(bie, ggq):
+    ctx = bie.Context()
+    sp, Np, Mt, k = SPECS[0]
+    s = bie.Surface(ctx, sp, Np, Mt, ggq)
+    slot = 16 * 48 * Mt * Np
+    W = torch.zeros((2, slot, Mt), dtype=torch.complex128, device="cuda")
+    band = torch.zeros((1, 16 * Mt, 3, 16 * Mt), dtype=torch.complex128, device="cuda")
+    plan_k = bie.Batch(ctx, [s], [k], bie.KERNEL_S | bie.KERNEL_K, W, slot)
+    with pytest.raises(RuntimeError):
+        plan_k.set_fill(band, 1)
+    plan = bie.Batch(ctx, [s], [k], bie.KERNEL_S, W[:1], slot)
+    plan.set_fill(band, 1)
+    launches_with = plan.config["launches"]
+    plan.set_fill(None, 0)
+    assert plan.config["launches"] == launches_with - Np
+    plan.run()
+    ctx.sync()
