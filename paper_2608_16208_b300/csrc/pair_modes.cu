@@ -599,10 +599,14 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
 // pair j of the batch: rho^2 on the ring at R2 + j Mt (single layer; shared memory with the double
 // layer); e^{i l a} at E + 33 j (single layer); A_m at Ab + j a_ps + m a_ms (double words for the
 // single layer); D_m at scrD + j + 32 m (double layer).
+// nlist: this warp's shared-memory list of kNearList near samples (single layer), or null: the
+// samples of phase A that take the cancellation-free difference are then collected over the batch's
+// pairs and evaluated with every lane busy (one lane per sample) instead of one pair at a time.
+constexpr int kNearList = 256;
 template <bool kWithK>
 __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, int64_t p0, int nb, double* R2,
                                             float4* E, double* Ab, int a_ps, int a_ms, double* scrD, PairInfo& mine,
-                                            unsigned& valid_mask) {
+                                            unsigned& valid_mask, int* nlist = nullptr) {
   const int lane = threadIdx.x & 31;
   const int Mt = a.Mt, L = a.L;
   constexpr bool wantK = kWithK;
@@ -647,41 +651,113 @@ __device__ __forceinline__ void front_batch(const PairArgs& a, const Smem& sm, i
     }
     valid_mask = __ballot_sync(0xffffffffu, lane < nb && mine.valid);
     // ---------------- A. grid minimiser (warp per pair); rho^2 kept for the single layer
-    for (int pi = 0; pi < nb; ++pi) {
-      const PairInfo pr = bcast(mine, pi);
-      if (!pr.valid) continue;
-      double* rho2 = wantK ? (double*)sm.W0 : R2 + pi * Mt;
-      const double* rr = a.ring_r + pr.ring * 3 * Mt;
-      const int i = (int)(pr.row % Mt);
-      const double dts = fabs(pr.t - pr.ts);
-      // |t - t_s| + |th_i - th_q| <= kStableDelta as a bound on the grid distance |i - q| (both
-      // branches give rho^2 to rounding, so the boundary only picks the cheaper formula)
-      const int kn = dts <= kStableDelta ? (int)((kStableDelta - dts) * Mt / kTwoPi) : -1;
-      double bv = INFINITY;
-      for (int q = lane; q < Mt; q += 32) {
-        const double thq = a.thg[3 * q];
-        const int dq = q > i ? q - i : i - q;
-        const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
-        double r2 = yx * yx + yy * yy + yz * yz;
-        if (min(dq, Mt - dq) <= kn || r2 <= kStableDist * kStableDist) {
-          const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
-          r2 = dot(Y, Y);
+    if (!wantK && nlist) {
+      // A1. rho^2 by plain subtraction on every sample; the samples near the target (those that take the
+      // cancellation-free difference) go to the list, or are evaluated here once the list is full
+      int nn = 0;
+      for (int pi = 0; pi < nb; ++pi) {
+        const PairInfo pr = bcast(mine, pi);
+        if (!pr.valid) continue;
+        double* rho2 = R2 + pi * Mt;
+        const double* rr = a.ring_r + pr.ring * 3 * Mt;
+        const int i = (int)(pr.row % Mt);
+        const double dts = fabs(pr.t - pr.ts);
+        const int kn = dts <= kStableDelta ? (int)((kStableDelta - dts) * Mt / kTwoPi) : -1;
+        for (int q0 = 0; q0 < Mt; q0 += 32) {
+          const int q = q0 + lane;
+          bool nr = false;
+          if (q < Mt) {
+            const int dq = q > i ? q - i : i - q;
+            const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
+            const double r2 = yx * yx + yy * yy + yz * yz;
+            nr = min(dq, Mt - dq) <= kn || r2 <= kStableDist * kStableDist;
+            rho2[q] = r2;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, nr);
+          if (nr) {
+            const int slot = nn + __popc(m & ((1u << lane) - 1u));
+            if (slot < kNearList) {
+              nlist[slot] = (pi << 16) | q;
+            } else {
+              const R3 Y = diff_ana<double>(a.S, pr.ts, a.thg[3 * q], pr.t, pr.th);
+              rho2[q] = dot(Y, Y);
+            }
+          }
+          nn += __popc(m);
         }
-        rho2[q] = r2;
-        bv = fmin(bv, r2);
       }
-      for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
       __syncwarp();
-      int bkey = 0x7fffffff;
-      const double tie = bv * (1 + 1e-12);
-      for (int q = lane; q < Mt; q += 32)
-        if (rho2[q] <= tie) {
-          const int dq = q > i ? q - i : i - q;
-          bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
+      // A2. the listed samples, one per lane
+      const int nl = min(nn, kNearList);
+      for (int b0 = 0; b0 < nl; b0 += 32) {
+        const int e = b0 + lane;
+        const int code = e < nl ? nlist[e] : 0;
+        const int pi = code >> 16, q = code & 0xffff;
+        const double ts = __shfl_sync(0xffffffffu, mine.ts, pi), t = __shfl_sync(0xffffffffu, mine.t, pi);
+        const double th = __shfl_sync(0xffffffffu, mine.th, pi);
+        if (e < nl) {
+          const R3 Y = diff_ana<double>(a.S, ts, a.thg[3 * q], t, th);
+          R2[pi * Mt + q] = dot(Y, Y);
         }
-      for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
-      if (lane == pi) mine.bi = bkey % Mt;
+      }
       __syncwarp();
+      // A3. grid minimiser of each pair (near-ties to the sample nearest the target, then the lower index)
+      for (int pi = 0; pi < nb; ++pi) {
+        const PairInfo pr = bcast(mine, pi);
+        if (!pr.valid) continue;
+        const double* rho2 = R2 + pi * Mt;
+        const int i = (int)(pr.row % Mt);
+        double bv = INFINITY;
+        for (int q = lane; q < Mt; q += 32) bv = fmin(bv, rho2[q]);
+        for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+        int bkey = 0x7fffffff;
+        const double tie = bv * (1 + 1e-12);
+        for (int q = lane; q < Mt; q += 32)
+          if (rho2[q] <= tie) {
+            const int dq = q > i ? q - i : i - q;
+            bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
+          }
+        for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
+        if (lane == pi) mine.bi = bkey % Mt;
+        __syncwarp();
+      }
+    } else {
+      for (int pi = 0; pi < nb; ++pi) {
+        const PairInfo pr = bcast(mine, pi);
+        if (!pr.valid) continue;
+        double* rho2 = wantK ? (double*)sm.W0 : R2 + pi * Mt;
+        const double* rr = a.ring_r + pr.ring * 3 * Mt;
+        const int i = (int)(pr.row % Mt);
+        const double dts = fabs(pr.t - pr.ts);
+        // |t - t_s| + |th_i - th_q| <= kStableDelta as a bound on the grid distance |i - q| (both
+        // branches give rho^2 to rounding, so the boundary only picks the cheaper formula)
+        const int kn = dts <= kStableDelta ? (int)((kStableDelta - dts) * Mt / kTwoPi) : -1;
+        double bv = INFINITY;
+        for (int q = lane; q < Mt; q += 32) {
+          const double thq = a.thg[3 * q];
+          const int dq = q > i ? q - i : i - q;
+          const double yx = rr[3 * q] - pr.x, yy = rr[3 * q + 1] - pr.y, yz = rr[3 * q + 2] - pr.z;
+          double r2 = yx * yx + yy * yy + yz * yz;
+          if (min(dq, Mt - dq) <= kn || r2 <= kStableDist * kStableDist) {
+            const R3 Y = diff_ana<double>(a.S, pr.ts, thq, pr.t, pr.th);
+            r2 = dot(Y, Y);
+          }
+          rho2[q] = r2;
+          bv = fmin(bv, r2);
+        }
+        for (int o = 16; o; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+        __syncwarp();
+        int bkey = 0x7fffffff;
+        const double tie = bv * (1 + 1e-12);
+        for (int q = lane; q < Mt; q += 32)
+          if (rho2[q] <= tie) {
+            const int dq = q > i ? q - i : i - q;
+            bkey = min(bkey, min(dq, Mt - dq) * Mt + q);
+          }
+        for (int o = 16; o; o >>= 1) bkey = min(bkey, __shfl_xor_sync(0xffffffffu, bkey, o));
+        if (lane == pi) mine.bi = bkey % Mt;
+        __syncwarp();
+      }
     }
     // ---------------- B. complex root and C. A_m, D_m (lane per pair)
     if (lane < nb && mine.valid) {
@@ -1138,6 +1214,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock, 1) pair_kernel(const _
 // words, shared-memory FFTs).  Each kernel gets its own register and occupancy budget.  Both cover
 // the pairs [c0, c0 + cn) of the launch; the record of pair p is p - c0.
 __global__ void __launch_bounds__(128, 4) pair_root_kernel(const __grid_constant__ PairArgs a, int64_t c0, int64_t cn) {
+  __shared__ int near_list[4][kNearList];   // phase A's near samples, per warp
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1148,7 +1225,7 @@ __global__ void __launch_bounds__(128, 4) pair_root_kernel(const __grid_constant
     PairInfo mine;
     unsigned vm;
     front_batch<false>(a, Smem{}, p0, nb, a.rec_R2 + r0 * Mt, a.rec_E + r0 * 33, a.rec_A + r0 * (L + 1), L + 1, 1,
-                       nullptr, mine, vm);
+                       nullptr, mine, vm, near_list[threadIdx.x >> 5]);
     if (lane < nb) {
       double* h = a.rec_hdr + (r0 + lane) * 8;
       h[0] = mine.a;
@@ -1565,6 +1642,7 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
 __global__ void __launch_bounds__(128, 4)
     pair_root_batch_kernel(const PairArgs* __restrict__ surfs, const BatchItem* __restrict__ items, int it0, int nit,
                            int item_pairs, const BatchRec rec) {
+  __shared__ int near_list[4][kNearList];   // phase A's near samples, per warp
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1579,7 +1657,7 @@ __global__ void __launch_bounds__(128, 4)
     PairInfo mine;
     unsigned vm;
     front_batch<false>(a, Smem{}, item.p0 + off, nb, rec.R2 + r0 * rec.Mt, rec.E + r0 * 33, rec.A + r0 * (rec.L + 1),
-                       rec.L + 1, 1, nullptr, mine, vm);
+                       rec.L + 1, 1, nullptr, mine, vm, near_list[threadIdx.x >> 5]);
     if (lane < nb) {
       double* h = rec.hdr + (r0 + lane) * 8;
       h[0] = mine.a;
