@@ -1400,9 +1400,12 @@ static bie_status launch_pairs_split(bie_surface s, PairArgs& a) {
   // the most resident warps
   auto tkern = a.fp64_transforms ? pair_transform_kernel<ArF64> : pair_transform_kernel<ArDW>;
   const size_t per_w = smem_doubles(a.Mt, a.P, a.L, false) * sizeof(double);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, tkern);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes(pair transform kernel)");
   int wpb = 0, best_w = 0, per_t = 0;
   for (int w = kMaxWarpsPerBlock; w >= 1; w /= 2) {
-    if (per_w * w > kSmemLimit) continue;
+    if (per_w * w > kSmemLimit || 32 * w > fa.maxThreadsPerBlock) continue;
     if (cudaFuncSetAttribute(tkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_w * w)) != cudaSuccess)
       continue;
     int nb = 0;
