@@ -369,65 +369,104 @@ __host__ __device__ inline FFTPlan make_plan(int n) {
   return p;
 }
 
+// One stage per radix, each butterfly's inputs held in named registers (a runtime-indexed array
+// would live in local memory); the stage index j = q Ns + jm by shift and mask when Ns is a power
+// of two.  The twiddle index r jm T / (Ns R) stays below T.
+__device__ __forceinline__ cplx tw64(const cplx* __restrict__ tw, int idx, int sign) {
+  const double2 w2 = __ldg(reinterpret_cast<const double2*>(tw) + idx);
+  return C(w2.x, sign > 0 ? -w2.y : w2.y);
+}
+
 // In-place (returns pointer to the buffer holding the result) transform of x[0..n)
 // using y as scratch.  sign = -1: X_k = sum x_j e^{-2 pi i jk/n}; sign = +1: inverse
-// (unnormalised).  Called by all 32 lanes of a warp.
-static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cplx* __restrict__ tw, int T, int sign) {
+// (unnormalised).  Called by all 32 lanes of a warp.  st0 > 0: the first st0 stages are done (x
+// holds their output).
+static __device__ __noinline__ cplx* warp_fft(cplx* x, cplx* y, int n, const cplx* __restrict__ tw, int T, int sign,
+                                              int st0 = 0) {
   const int lane = threadIdx.x & 31;
   const FFTPlan p = make_plan(n);
   cplx* src = x;
   cplx* dst = y;
   int Ns = 1;
+  for (int st = 0; st < st0; ++st) Ns *= p.rad[st];
   const double s3 = 0.86602540378443864676 * sign;
-  for (int st = 0; st < p.nst; ++st) {
+  for (int st = st0; st < p.nst; ++st) {
     const int R = p.rad[st];
     const int stride = n / R;
-    const int tstep = (T / n) * (n / (Ns * R));  // table index step per (r * jm)
-    for (int j = lane; j < stride; j += 32) {
-      const int jm = j % Ns;
-      cplx v[5];
-      for (int r = 0; r < R; ++r) {
-        cplx a = src[j + r * stride];
-        if (r && jm) {
-          const double2 w2 = __ldg(reinterpret_cast<const double2*>(tw) + (r * jm * tstep) % T);
-          cplx w = C(w2.x, sign > 0 ? -w2.y : w2.y);
-          a = a * w;
+    const int tstep = (T / n) * (n / (Ns * R));
+    const int sh = (Ns & (Ns - 1)) == 0 ? __ffs(Ns) - 1 : -1;
+    if (R == 4) {
+      for (int j = lane; j < stride; j += 32) {
+        const int jm = sh >= 0 ? (j & (Ns - 1)) : j % Ns;
+        const int q = sh >= 0 ? (j >> sh) : j / Ns;
+        cplx v0 = src[j], v1 = src[j + stride], v2 = src[j + 2 * stride], v3 = src[j + 3 * stride];
+        if (jm) {
+          v1 = v1 * tw64(tw, jm * tstep, sign);
+          v2 = v2 * tw64(tw, 2 * jm * tstep, sign);
+          v3 = v3 * tw64(tw, 3 * jm * tstep, sign);
         }
-        v[r] = a;
+        const cplx s02 = v0 + v2, d02 = v0 - v2, s13 = v1 + v3, d13 = v1 - v3;
+        const cplx jd = sign < 0 ? C(d13.im, -d13.re) : C(-d13.im, d13.re);   // sign i d13
+        const int idx = q * Ns * 4 + jm;
+        dst[idx] = s02 + s13;
+        dst[idx + Ns] = d02 + jd;
+        dst[idx + 2 * Ns] = s02 - s13;
+        dst[idx + 3 * Ns] = d02 - jd;
       }
-      cplx o[5];
-      if (R == 5) {
-        // DFT of length 5: cos and sin of 2 pi / 5 and 4 pi / 5
-        const double c1 = 0.30901699437494742, c2 = -0.80901699437494742;
-        const double s1 = 0.95105651629515357 * sign, s2 = 0.58778525229247313 * sign;
-        const cplx t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
-        const cplx a1 = v[0] + c1 * t1 + c2 * t2, a2 = v[0] + c2 * t1 + c1 * t2;
+    } else if (R == 2) {
+      for (int j = lane; j < stride; j += 32) {
+        const int jm = sh >= 0 ? (j & (Ns - 1)) : j % Ns;
+        const int q = sh >= 0 ? (j >> sh) : j / Ns;
+        const cplx v0 = src[j];
+        cplx v1 = src[j + stride];
+        if (jm) v1 = v1 * tw64(tw, jm * tstep, sign);
+        const int idx = q * Ns * 2 + jm;
+        dst[idx] = v0 + v1;
+        dst[idx + Ns] = v0 - v1;
+      }
+    } else if (R == 5) {
+      // DFT of length 5: cos and sin of 2 pi / 5 and 4 pi / 5
+      const double c1 = 0.30901699437494742, c2 = -0.80901699437494742;
+      const double s1 = 0.95105651629515357 * sign, s2 = 0.58778525229247313 * sign;
+      for (int j = lane; j < stride; j += 32) {
+        const int jm = sh >= 0 ? (j & (Ns - 1)) : j % Ns;
+        const int q = sh >= 0 ? (j >> sh) : j / Ns;
+        const cplx v0 = src[j];
+        cplx v1 = src[j + stride], v2 = src[j + 2 * stride], v3 = src[j + 3 * stride], v4 = src[j + 4 * stride];
+        if (jm) {
+          v1 = v1 * tw64(tw, jm * tstep, sign);
+          v2 = v2 * tw64(tw, 2 * jm * tstep, sign);
+          v3 = v3 * tw64(tw, 3 * jm * tstep, sign);
+          v4 = v4 * tw64(tw, 4 * jm * tstep, sign);
+        }
+        const cplx t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4, t4 = v2 - v3;
+        const cplx a1 = v0 + c1 * t1 + c2 * t2, a2 = v0 + c2 * t1 + c1 * t2;
         const cplx b1 = s1 * t3 + s2 * t4, b2 = s2 * t3 - s1 * t4;   // times i below
-        o[0] = v[0] + t1 + t2;
-        o[1] = a1 + C(-b1.im, b1.re);
-        o[4] = a1 - C(-b1.im, b1.re);
-        o[2] = a2 + C(-b2.im, b2.re);
-        o[3] = a2 - C(-b2.im, b2.re);
-      } else if (R == 4) {
-        cplx s02 = v[0] + v[2], d02 = v[0] - v[2], s13 = v[1] + v[3], d13 = v[1] - v[3];
-        cplx jd = sign < 0 ? C(d13.im, -d13.re) : C(-d13.im, d13.re);  // sign*i*d13
-        o[0] = s02 + s13;
-        o[2] = s02 - s13;
-        o[1] = d02 + jd;
-        o[3] = d02 - jd;
-      } else if (R == 2) {
-        o[0] = v[0] + v[1];
-        o[1] = v[0] - v[1];
-      } else {
-        cplx t1 = v[1] + v[2], d = v[1] - v[2];
-        cplx t2 = C(-s3 * d.im, s3 * d.re);
-        cplx base = v[0] - 0.5 * t1;
-        o[0] = v[0] + t1;
-        o[1] = base + t2;
-        o[2] = base - t2;
+        const int idx = q * Ns * 5 + jm;
+        dst[idx] = v0 + t1 + t2;
+        dst[idx + Ns] = a1 + C(-b1.im, b1.re);
+        dst[idx + 4 * Ns] = a1 - C(-b1.im, b1.re);
+        dst[idx + 2 * Ns] = a2 + C(-b2.im, b2.re);
+        dst[idx + 3 * Ns] = a2 - C(-b2.im, b2.re);
       }
-      const int idx = (j / Ns) * Ns * R + jm;
-      for (int r = 0; r < R; ++r) dst[idx + r * Ns] = o[r];
+    } else {
+      for (int j = lane; j < stride; j += 32) {
+        const int jm = sh >= 0 ? (j & (Ns - 1)) : j % Ns;
+        const int q = sh >= 0 ? (j >> sh) : j / Ns;
+        const cplx v0 = src[j];
+        cplx v1 = src[j + stride], v2 = src[j + 2 * stride];
+        if (jm) {
+          v1 = v1 * tw64(tw, jm * tstep, sign);
+          v2 = v2 * tw64(tw, 2 * jm * tstep, sign);
+        }
+        const cplx t1 = v1 + v2, d = v1 - v2;
+        const cplx t2 = C(-s3 * d.im, s3 * d.re);
+        const cplx base = v0 - 0.5 * t1;
+        const int idx = q * Ns * 3 + jm;
+        dst[idx] = v0 + t1;
+        dst[idx + Ns] = base + t2;
+        dst[idx + 2 * Ns] = base - t2;
+      }
     }
     __syncwarp();
     cplx* tmp = src;

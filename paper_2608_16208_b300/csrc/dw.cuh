@@ -183,16 +183,18 @@ struct StageIdx {
   __device__ __forceinline__ int quo(int j) const { return sh >= 0 ? (j >> sh) : j / Ns; }
 };
 
+// st0 > 0: the first st0 stages are done (x holds their output).
 static __device__ __noinline__ float4* warp_fft_dw(float4* x, float4* y, int n, const float4* __restrict__ tw, int T,
-                                                   int sign) {
+                                                   int sign, int st0 = 0) {
   const int lane = threadIdx.x & 31;
   const FFTPlan p = make_plan(n);
   float4* src = x;
   float4* dst = y;
   int Ns = 1;
+  for (int st = 0; st < st0; ++st) Ns *= p.rad[st];
   // sign * sqrt(3)/2 as a double word
   const float2 s3 = make_float2(sign * 0.8660253882408142f, sign * 1.5543625053737742e-08f);
-  for (int st = 0; st < p.nst; ++st) {
+  for (int st = st0; st < p.nst; ++st) {
     const int R = p.rad[st];
     const int stride = n / R;
     const int tstep = (T / n) * (n / (Ns * R));   // r * jm * tstep < T

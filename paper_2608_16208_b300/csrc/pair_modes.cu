@@ -244,22 +244,25 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 // v mod n for |v| < n
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// sin(k x) - k sin(x), k >= 0, without cancellation (series when k x < 1).
-__device__ inline double sin_k_minus(int k, double x) {
+// sin(k x) - k sin(x), k >= 0, without cancellation: the Taylor series when |k x| < 1 (its term
+// ratios are constants once the loop unrolls), else from skx = sin(k x) and sx = sin(x).
+__device__ inline double sin_k_minus(int k, double x, double skx, double sx) {
   const double kx = k * x;
   if (fabs(kx) < 1.0) {
     const double kx2 = kx * kx, x2 = x * x;
-    double an = kx * kx2 / 6.0, bn = k * x * x2 / 6.0, acc = 0.0, sg = -1.0;
+    constexpr double r6 = 1.0 / 6.0;
+    double an = kx * kx2 * r6, bn = k * x * x2 * r6, acc = 0.0, sg = -1.0;
+#pragma unroll
     for (int n = 1; n <= 12; ++n) {
       acc += sg * (an - bn);
-      const double den = (2.0 * n + 2) * (2.0 * n + 3);
-      an *= kx2 / den;
-      bn *= x2 / den;
+      const double rden = 1.0 / ((2.0 * n + 2) * (2.0 * n + 3));
+      an *= kx2 * rden;
+      bn *= x2 * rden;
       sg = -sg;
     }
     return acc;
   }
-  return sin(kx) - k * sin(x);
+  return skx - k * sx;
 }
 
 struct Smem {
@@ -332,18 +335,56 @@ __device__ __noinline__ cplx* warp_fft_x(cplx* x, cplx* y, int n, const float4* 
 
 // e^{ija} Z_j / Mt (j = -M..M, Nyquist split evenly) placed on the P grid in X, inverse
 // transform with scratch Y (in double words if dw); returns the buffer holding the result.
+// The modes sit at |j| <= M of the length-P input, so where the transform's first stage is radix 4
+// with stride s = P/4 > M, its butterfly j < s meets at most x_j (j <= M) and x_{j+3s} (j >= s - M):
+// that stage runs here, fused with the placement and without the zeros (the same values).
 __device__ __noinline__ cplx* upsample(const cplx* Z, const cplx* ph, cplx* X, cplx* Y, int Mt, int P, const cplx* tw,
                                  const float4* twf, int T, bool dw) {
   const int lane = threadIdx.x & 31;
   const int M = Mt / 2;
-  for (int pp = lane; pp < P; pp += 32) X[pp] = C(0.0);
-  __syncwarp();
-  for (int jj = lane; jj <= 2 * M; jj += 32) {
-    const int jv = jj - M;
+  auto mode_at = [&](int jv) {
     cplx z = Z[wrapi(jv, Mt)] * (1.0 / Mt);
     if (jv == M || jv == -M) z = 0.5 * z;
-    X[wrapi(jv, P)] = ph[jj] * z;
+    return ph[jv + M] * z;
+  };
+  const int s4 = P / 4;
+  if (P % 4 == 0 && s4 > M) {
+    if (dw) {
+      float4* Xf = reinterpret_cast<float4*>(X);
+      for (int j = lane; j < s4; j += 32) {
+        const float4 v0 = j <= M ? dwc_from(mode_at(j)) : dwc_zero();
+        const float4 v3 = j >= s4 - M ? dwc_from(mode_at(j - s4)) : dwc_zero();
+        const float4 jd = mul_i(dwc_sub(dwc_zero(), v3), +1);
+        Xf[4 * j] = dwc_add(v0, v3);
+        Xf[4 * j + 1] = dwc_add(v0, jd);
+        Xf[4 * j + 2] = dwc_sub(v0, v3);
+        Xf[4 * j + 3] = dwc_sub(v0, jd);
+      }
+      __syncwarp();
+      float4* r = warp_fft_dw(Xf, reinterpret_cast<float4*>(Y), P, twf, T, +1, 1);
+      cplx* rc = reinterpret_cast<cplx*>(r);
+      for (int i = lane; i < P; i += 32) {
+        const float4 v = r[i];
+        rc[i] = dwc_to(v);
+      }
+      __syncwarp();
+      return rc;
+    }
+    for (int j = lane; j < s4; j += 32) {
+      const cplx v0 = j <= M ? mode_at(j) : C(0.0);
+      const cplx v3 = j >= s4 - M ? mode_at(j - s4) : C(0.0);
+      const cplx jd = C(v3.im, -v3.re);   // +i (x_{j+s} - x_{j+3s})
+      X[4 * j] = v0 + v3;
+      X[4 * j + 1] = v0 + jd;
+      X[4 * j + 2] = v0 - v3;
+      X[4 * j + 3] = v0 - jd;
+    }
+    __syncwarp();
+    return warp_fft(X, Y, P, tw, T, +1, 1);
   }
+  for (int pp = lane; pp < P; pp += 32) X[pp] = C(0.0);
+  __syncwarp();
+  for (int jj = lane; jj <= 2 * M; jj += 32) X[wrapi(jj - M, P)] = mode_at(jj - M);
   __syncwarp();
   return dw ? warp_fft_x(X, Y, P, twf, T, +1) : warp_fft(X, Y, P, tw, T, +1);
 }
@@ -362,6 +403,8 @@ struct ArDW {
   static __device__ __forceinline__ C mulr(C x, R r) { return dwc_mulr(x, r); }
   static __device__ __forceinline__ C conjg(C x) { return dwc_conj(x); }
   static __device__ __forceinline__ C add(C x, C y) { return dwc_add(x, y); }
+  static __device__ __forceinline__ C sub(C x, C y) { return dwc_sub(x, y); }
+  static __device__ __forceinline__ C jneg(C x) { return mul_i(dwc_sub(dwc_zero(), x), +1); }   // i (0 - x)
   static __device__ __forceinline__ C half(C x) { return dwc_scale2(x, 0.5f); }
   static __device__ __forceinline__ C zero() { return dwc_zero(); }
   static __device__ __forceinline__ C mk(R re, R im) { return mkc(re, im); }
@@ -378,8 +421,8 @@ struct ArDW {
   }
   static __device__ __forceinline__ double lead(R x) { return (double)x.x; }
   static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { dw_sincos(x, s, c); }
-  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign) {
-    return warp_fft_dw(x, y, n, a.twf, a.T, sign);
+  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign, int st0 = 0) {
+    return warp_fft_dw(x, y, n, a.twf, a.T, sign, st0);
   }
 };
 struct ArF64 {
@@ -392,6 +435,8 @@ struct ArF64 {
   static __device__ __forceinline__ C mulr(C x, R r) { return x * r; }
   static __device__ __forceinline__ C conjg(C x) { return conj(x); }
   static __device__ __forceinline__ C add(C x, C y) { return x + y; }
+  static __device__ __forceinline__ C sub(C x, C y) { return x - y; }
+  static __device__ __forceinline__ C jneg(C x) { return bie::C(x.im, -x.re); }   // i (0 - x)
   static __device__ __forceinline__ C half(C x) { return 0.5 * x; }
   static __device__ __forceinline__ C zero() { return bie::C(0.0); }
   static __device__ __forceinline__ C mk(R re, R im) { return bie::C(re, im); }
@@ -405,8 +450,8 @@ struct ArF64 {
   static __device__ __forceinline__ C imscale(C x, int e) { return bie::C(x.re, ldexp(x.im, e)); }
   static __device__ __forceinline__ double lead(R x) { return x; }
   static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { sincos(x, s, c); }
-  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign) {
-    return warp_fft(x, y, n, a.tw, a.T, sign);
+  static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign, int st0 = 0) {
+    return warp_fft(x, y, n, a.tw, a.T, sign, st0);
   }
 };
 
@@ -482,19 +527,38 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       snw[q] = Ar::rmul(skr, Ar::rfrom(rinv));
     }
     __syncwarp();
-    // ---- modes of F and cos(k rho); upsample onto the shifted P grid
+    // ---- modes of F and cos(k rho); upsample onto the shifted P grid.  The modes sit at |j| <= M of
+    // the length-P input: where the first stage is radix 4 with stride s = P/4 > M, its butterfly
+    // j < s meets at most x_j (j <= M) and x_{j+3s} (j >= s - M), and it runs here, fused with the
+    // placement and without the zeros (the same values)
     Cx* Z1 = Ar::fft(W0, W1, Mt, a, -1);
     Cx* X = (Z1 == W0) ? W1 : W0;
-    for (int pp = lane; pp < P; pp += 32) X[pp] = Ar::zero();
-    __syncwarp();
-    for (int jj = lane; jj <= 2 * M; jj += 32) {
-      const int jv = jj - M;
-      Cx z = Ar::mul(phase(jj), Z1[wrap1(jv, Mt)]);
+    auto mode_at = [&](int jv) {
+      Cx z = Ar::mul(phase(jv + M), Z1[wrap1(jv, Mt)]);
       if (jv == M || jv == -M) z = Ar::half(z);
-      X[wrap1(jv, P)] = z;
+      return z;
+    };
+    Cx* up1;   // re: F~, im: C~
+    const int s4 = P / 4;
+    if (P % 4 == 0 && s4 > M) {
+      for (int j = lane; j < s4; j += 32) {
+        const Cx v0 = j <= M ? mode_at(j) : Ar::zero();
+        const Cx v3 = j >= s4 - M ? mode_at(j - s4) : Ar::zero();
+        const Cx jd = Ar::jneg(v3);
+        X[4 * j] = Ar::add(v0, v3);
+        X[4 * j + 1] = Ar::add(v0, jd);
+        X[4 * j + 2] = Ar::sub(v0, v3);
+        X[4 * j + 3] = Ar::sub(v0, jd);
+      }
+      __syncwarp();
+      up1 = Ar::fft(X, Z1, P, a, +1, 1);
+    } else {
+      for (int pp = lane; pp < P; pp += 32) X[pp] = Ar::zero();
+      __syncwarp();
+      for (int jj = lane; jj <= 2 * M; jj += 32) X[wrap1(jj - M, P)] = mode_at(jj - M);
+      __syncwarp();
+      up1 = Ar::fft(X, Z1, P, a, +1);
     }
-    __syncwarp();
-    Cx* up1 = Ar::fft(X, Z1, P, a, +1);   // re: F~, im: C~
     Cx* uf = (up1 == W0) ? W1 : W0;
     // ---- U = F~ C~ Acal in the real part, the next valid pair's circulant in the imaginary part.
     // Each part comes out of the shared transform with an error in proportion to the other's size
@@ -864,8 +928,13 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
       const double qb = exp(-rb), om = -expm1(-rb);
       const bool translated = rb < kSmallB;
       // ---- D1. phases e^{ija}, each from its own sincos: the translated tau_3 combines
-      // phase-weighted terms that cancel, so a rotation recurrence's ulp drift would be amplified
-      for (int jj = lane; jj <= 2 * M; jj += 32) sm.ph[jj] = cexpi((jj - M) * ra);
+      // phase-weighted terms that cancel, so a rotation recurrence's ulp drift would be amplified;
+      // e^{-ija} is the conjugate (sin odd, cos even)
+      for (int j = lane; j <= M; j += 32) {
+        const cplx e = cexpi(j * ra);
+        sm.ph[M - j] = conj(e);
+        sm.ph[M + j] = e;
+      }
       // A_m and B_m(0,b) = -(m - 1/2) e^b (D_m + 2 sinh^2(b/2) A_m) / sinh^2 b from the scratch
       const double shb = sinh(rb), sh2b = sinh(0.5 * rb) * sinh(0.5 * rb);
       const double fac = exp(rb) / (shb * shb);
@@ -943,8 +1012,9 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           al = a.k * a.k * sa;
           be = a.k * a.k * a.k * sb;
         } else {
-          al = (1 - ckr - x * skr) / r2;
-          be = (skr - x * ckr) / (r2 * rho);
+          const double ri2 = rinv * rinv;   // 1 / rho^2 from the rsqrt already taken (no division)
+          al = (1 - ckr - x * skr) * ri2;
+          be = (skr - x * ckr) * (ri2 * rinv);
         }
         // tau_0 = nu(y) . (y - x) (K: the source normal) or nu(x) . (x - y) (K': the target's normal);
         // near ones are replaced below
@@ -1110,24 +1180,30 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
           sm.tau0[q] = (fabs(phq) < kNearPhi) ? 0.0 : (sm.hr[q] - H3a - H3pa * sin(phq)) / s2;
         }
         __syncwarp();
-        for (int q = 0; q < Mt; ++q) {
+        // only the grid angles within kNearPhi of a: those next to the nearest one
+        const int qc = (int)rint(ra * (Mt / kTwoPi));
+        const int qr = (int)(kNearPhi * Mt / kTwoPi) + 2;
+        for (int dq = -qr; dq <= qr; ++dq) {
+          const int q = wrapi(qc + dq, Mt);
           const double phq = wrap_pi(kTwoPi * q / Mt - ra);
           if (!(fabs(phq) < kNearPhi)) continue;
-          const double s2 = sin(0.5 * phq) * sin(0.5 * phq);
+          const double sh = sin(0.5 * phq), s2 = sh * sh, rs2 = 1.0 / s2, sph = sin(phq);
+          // modes k and -k share |k|'s factors (the real one even, the imaginary one odd in k);
+          // k = 0 contributes nothing
           double acc = 0.0;
-          for (int jj = lane; jj <= 2 * M; jj += 32) {
-            const int kv = jj - M, ka = kv < 0 ? -kv : kv;
-            const cplx hv = sm.kk[jj] * sm.ph[jj];   // h3_k e^{ika}
+          for (int ka = lane + 1; ka <= M; ka += 32) {
+            const cplx hp = sm.kk[M + ka] * sm.ph[M + ka], hm = sm.kk[M - ka] * sm.ph[M - ka];   // h3_k e^{ika}
             double gre, gim;
             if (s2 == 0.0) {
               gre = -2.0 * ka * ka;
               gim = 0.0;
             } else {
-              const double sk = sin(0.5 * ka * phq);
-              gre = -2.0 * sk * sk / s2;
-              gim = (kv < 0 ? -1.0 : 1.0) * sin_k_minus(ka, phq) / s2;
+              double sk, ck;   // sin, cos of k phq / 2; sin(k phq) = 2 sk ck
+              sincos(0.5 * ka * phq, &sk, &ck);
+              gre = -2.0 * sk * sk * rs2;
+              gim = sin_k_minus(ka, phq, 2.0 * sk * ck, sph) * rs2;
             }
-            acc += hv.re * gre - hv.im * gim;
+            acc += (hp.re + hm.re) * gre - (hp.im - hm.im) * gim;
           }
           acc = warp_sum(acc);
           if (lane == 0) sm.tau0[q] = acc;
@@ -1145,14 +1221,24 @@ __device__ __forceinline__ void process_batch(const PairArgs& a, const Smem& sm,
         }
         __syncwarp();
       }
-      // ---- D9. upsample h3 (or d); B~ <- V_H = h3~ B~
+      // ---- D9. upsample h3 (or d); B~ <- V_H = h3~ B~.  The upsampled signal is real: with
+      // E_k = X_k + X_{k+P/2}, O_k = e^{2 pi i k / P} (X_k - X_{k+P/2}), the inverse transform of length
+      // P/2 of E + i O holds the even samples in its real parts and the odd ones in its imaginary
+      // parts, i.e. sample pp at double pp.  X_k = e^{ika} h_k sits at k <= M and P - M <= k.
       {
-        for (int pp = lane; pp < P; pp += 32) sm.W0[pp] = C(0.0);
+        const int P2 = P / 2;
+        for (int pp = lane; pp < P2; pp += 32) sm.W0[pp] = C(0.0);
         __syncwarp();
-        for (int jj = lane; jj <= 2 * M; jj += 32) sm.W0[wrapi(jj - M, P)] = sm.ph[jj] * sm.kk[jj];
+        for (int jj = lane; jj <= 2 * M; jj += 32) {
+          const int kv = jj - M;
+          const int kz = kv >= 0 ? kv : P2 + kv;
+          const cplx x = sm.ph[jj] * sm.kk[jj];
+          const cplx iw = C(0.0, kv >= 0 ? 1.0 : -1.0) * tw64(a.tw, kz * (a.T / P), +1);   // +-i e^{2 pi i kz / P}
+          sm.W0[kz] = x + iw * x;
+        }
         __syncwarp();
-        const cplx* up3 = warp_fft(sm.W0, sm.W1, P, a.tw, a.T, +1);
-        for (int pp = lane; pp < P; pp += 32) sm.Bcal[pp] = up3[pp].re * sm.Bcal[pp];
+        const double* up3 = reinterpret_cast<const double*>(warp_fft(sm.W0, sm.W1, P2, a.tw, a.T, +1));
+        for (int pp = lane; pp < P; pp += 32) sm.Bcal[pp] = up3[pp] * sm.Bcal[pp];
         __syncwarp();
       }
       // ---- D10. transform (V_K A~) + i (V_H), unpack AT1 and the tau_3 Toeplitz part

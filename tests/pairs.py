@@ -37,3 +37,25 @@ def sample_pairs(Np, Mt, n, seed=0):
                 rows.append(r)
                 srcs.append(s)
     return np.array(rows, dtype=np.int64), np.array(srcs, dtype=np.int32)
+
+
+def method_modes_chunk(args):
+    """Process-pool worker: the oracle's method-mode modes of one chunk of pairs,
+    args = (surface, t, th, t_s, Mt, k, kernels)."""
+    from oracle import kernel_modes as km
+    surface, t, th, ts, Mt, k, kernels = args
+    return km.method_modes(surface, t, th, ts, Mt, k, kernels)
+
+
+def ulp_sensitivity(surface, t, th, ts, Mt, k, kernel):
+    """Per pair, the largest normwise change of the oracle's modes when one of the pair's FP64
+    inputs (t, th, t_s) moves by one ulp: the floor below which two FP64 evaluations of the same
+    coefficients cannot be expected to agree."""
+    from oracle import kernel_modes as km
+    base = km.method_modes(surface, t, th, ts, Mt, k, (kernel,))[kernel]
+    nb = np.max(np.abs(base), axis=1)
+    out = np.zeros(len(t))
+    for tt, hh, ss in ((np.nextafter(t, 10), th, ts), (t, np.nextafter(th, 10), ts), (t, th, np.nextafter(ts, 10))):
+        v = km.method_modes(surface, tt, hh, ss, Mt, k, (kernel,))[kernel]
+        out = np.maximum(out, np.max(np.abs(v - base), axis=1) / nb)
+    return out
