@@ -139,23 +139,31 @@ __global__ void near_fill_kernel(int Np, int Mt, int periodic, int jpanel, cplx 
   const int64_t base = ((((int64_t)l * 3 + d) * 16) * Mt + i) * Mt;
   const double* cf = coef + ((d * 16 + l) * 16) * 16;   // [g][n]
   if constexpr (kDW) {
+    // thread per (source angle lp, group of npt source nodes n): the 16 weights of lp (one per GGQ
+    // node g) are loaded once and folded into the group's npt outputs (they were loaded once per output)
     const float2* cw = coefw + ((d * 16 + l) * 16) * 16;
     const float4* W = reinterpret_cast<const float4*>(WS);
     const float4 sw = dwc_from(sS);
-    for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
-      const int n = e / Mt, lp = e % Mt;
-      float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int g = 0; g < 16; ++g) {
-        const float4 w = W[base + (int64_t)g * Mt * Mt + lp];
-        const float2 c = cw[g * 16 + n];
-        ar = dw_add(ar, dw_mul(c, cre(w)));
-        ai = dw_add(ai, dw_mul(c, cim(w)));
+    const int npt = Mt >= 128 ? 8 : 4;
+    for (int it = threadIdx.x; it < (16 / npt) * Mt; it += blockDim.x) {
+      const int lp = it % Mt, n0 = (it / Mt) * npt;
+      float4 w[16];
+#pragma unroll
+      for (int g = 0; g < 16; ++g) w[g] = W[base + (int64_t)g * Mt * Mt + lp];
+      for (int n = n0; n < n0 + npt; ++n) {
+        float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+          const float2 c = cw[g * 16 + n];
+          ar = dw_add(ar, dw_mul(c, cre(w[g])));
+          ai = dw_add(ai, dw_mul(c, cim(w[g])));
+        }
+        const int e = n * Mt + lp;
+        float4 add = dwc_mul(sw, mkc(ar, ai));
+        if (jcol) add = dwc_mulr(add, dw_from(jcol[(int64_t)ip * 16 * Mt + e]));   // times J of the source node
+        const cplx ad = dwc_to(add);
+        Arow[e] = out.band ? ad : Arow[e] + ad;
       }
-      float4 add = dwc_mul(sw, mkc(ar, ai));
-      if (jcol) add = dwc_mulr(add, dw_from(jcol[(int64_t)ip * 16 * Mt + e]));   // times J of the source node
-      const cplx ad = dwc_to(add);
-      Arow[e] = out.band ? ad : Arow[e] + ad;
     }
   } else {
   for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
@@ -194,15 +202,19 @@ __global__ void near_fill_ring_kernel(int Np, int Mt, int periodic, int jpanel, 
   }
   const int64_t pp0 = (((int64_t)l * 3 + d) * 16) * Mt + i;   // pair (l, d, g = 0, i) of the panel
   const double* cf = coef + ((d * 16 + l) * 16) * 16;          // [g][n]
-  for (int e = threadIdx.x; e < 16 * Mt; e += blockDim.x) {
-    const int n = e / Mt, lp = e % Mt;
-    cplx acc = C(0.0);
-#pragma unroll 4
-    for (int g = 0; g < 16; ++g) {
-      const int64_t r = (pbase + pp0 + (int64_t)g * Mt) % ring;
-      acc = acc + cf[g * 16 + n] * W[r * w_ld + lp];
+  // thread per (source angle lp, group of npt source nodes n), as near_fill_kernel
+  const int npt = Mt >= 128 ? 8 : 4;
+  for (int it = threadIdx.x; it < (16 / npt) * Mt; it += blockDim.x) {
+    const int lp = it % Mt, n0 = (it / Mt) * npt;
+    cplx w[16];
+#pragma unroll
+    for (int g = 0; g < 16; ++g) w[g] = W[((pbase + pp0 + (int64_t)g * Mt) % ring) * w_ld + lp];
+    for (int n = n0; n < n0 + npt; ++n) {
+      cplx acc = C(0.0);
+#pragma unroll
+      for (int g = 0; g < 16; ++g) acc = acc + cf[g * 16 + n] * w[g];
+      Arow[n * Mt + lp] = sS * acc;
     }
-    Arow[e] = sS * acc;
   }
 }
 
