@@ -83,6 +83,18 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 __device__ __forceinline__ double dw_to(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
 
+// sqrt of a double word a >= 0 (Dekker's double-length square root, Numer. Math. 18, 1971): s =
+// sqrt(h) in FP32, then one Newton step on the residual a - s^2 with s^2 = p + e exact by FMA (h - p
+// is exact: p is within a few ulps of h); about 2^-47 relative.
+__device__ __forceinline__ float2 dw_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = __fsqrt_rn(a.x);
+  const float p = __fmul_rn(s, s);
+  const float e = fmaf(s, s, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), e), a.y);
+  return fast_two_sum(s, __fdividef(r, 2.f * s));
+}
+
 // complex helpers on float4 = (re.h, re.l, im.h, im.l)
 __device__ __forceinline__ float2 cre(float4 a) { return make_float2(a.x, a.y); }
 __device__ __forceinline__ float2 cim(float4 a) { return make_float2(a.z, a.w); }

@@ -237,6 +237,12 @@ __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restr
 }
 
 // ------------------------------------------------------------------ small helpers of phase D
+// sin x for |x| <= 0.05 by its Taylor polynomial through x^9 (the first omitted term is below
+// 2^-60 |x|): relative accuracy without the range reduction of the library sine.
+__device__ __forceinline__ double sin_small(double x) {
+  const double x2 = x * x;
+  return x * fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
+}
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -421,6 +427,11 @@ struct ArDW {
   }
   static __device__ __forceinline__ double lead(R x) { return (double)x.x; }
   static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { dw_sincos(x, s, c); }
+  // F = sqrt(s) / rho from s (FP64) and 1/rho (FP64 and in this form)
+  static __device__ __forceinline__ R smooth_f(double s, double rinv, R ri) {
+    (void)rinv;
+    return dw_mul(dw_sqrt(dw_from(s)), ri);
+  }
   static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign, int st0 = 0) {
     return warp_fft_dw(x, y, n, a.twf, a.T, sign, st0);
   }
@@ -450,6 +461,10 @@ struct ArF64 {
   static __device__ __forceinline__ C imscale(C x, int e) { return bie::C(x.re, ldexp(x.im, e)); }
   static __device__ __forceinline__ double lead(R x) { return x; }
   static __device__ __forceinline__ void sincosr(double x, R* s, R* c) { sincos(x, s, c); }
+  static __device__ __forceinline__ R smooth_f(double s, double rinv, R ri) {
+    (void)ri;
+    return sqrt(s) * rinv;
+  }
   static __device__ __forceinline__ C* fft(C* x, C* y, int n, const PairArgs& a, int sign, int st0 = 0) {
     return warp_fft(x, y, n, a.tw, a.T, sign, st0);
   }
@@ -518,13 +533,13 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
       const double rinv = rsqrt(r2);
       const double rho = r2 * rinv;
       const double dq = thq - pr.a;
-      const double sp = fabs(dq) < 0.1 ? sin(0.5 * dq) : a.thg[3 * q + 1] * pr.cha - a.thg[3 * q + 2] * pr.sha;
+      const double sp = fabs(dq) < 0.1 ? sin_small(0.5 * dq) : a.thg[3 * q + 1] * pr.cha - a.thg[3 * q + 2] * pr.sha;
       const double sv = pr.om * pr.om + 4 * pr.qb * sp * sp;
-      const double F = sqrt(sv) * rinv;
+      const Rx ri = Ar::rfrom(rinv);
       Rx skr, ckr;
       Ar::sincosr(a.k * rho, &skr, &ckr);
-      W0[q] = Ar::mk(Ar::rfrom(F), ckr);
-      snw[q] = Ar::rmul(skr, Ar::rfrom(rinv));
+      W0[q] = Ar::mk(Ar::smooth_f(sv, rinv, ri), ckr);
+      snw[q] = Ar::rmul(skr, ri);
     }
     __syncwarp();
     // ---- modes of F and cos(k rho); upsample onto the shifted P grid.  The modes sit at |j| <= M of
