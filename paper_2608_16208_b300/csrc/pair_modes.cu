@@ -179,7 +179,7 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
 }
 
 // ------------------------------------------------------------------ phase C: A_m, D_m (one lane)
-// rec[4m..4m+3] = (2m-1)/(2m+1), 8m/(2m+1), 4m/(2m-1), (2m+1)/(2m-1)
+// rec[4m..4m+3] = (2m-1)/(2m+1), 8m/(2m+1), t_m, w_m (Miller's rescaled recurrence; recurrence_table)
 __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restrict__ rec, int rec_len, double* A,
                                     double* D, int stride, bool dw_out) {
   // D may be null (only A is needed for the single-layer kernel); dw_out: A is left as double words
@@ -190,50 +190,56 @@ __device__ __noinline__ void a_modes_lane(double b, int L, const double* __restr
   const double A0 = 2 / kPi * K;
   const double sh2 = sinh(b / 2) * sinh(b / 2);
   if (L * b <= kForwardLimit) {
+    auto put = [&](int m, double v) {   // A_m, as a double word where asked
+      if (dw_out) reinterpret_cast<float2*>(A)[m * stride] = dw_from(v);
+      else A[m * stride] = v;
+    };
     double am = A0, dm = (2 / kPi) * ((K - E) / q - K);
-    A[0] = am;
+    put(0, am);
     if (D) D[0] = -dm;
     am += dm;
-    A[stride] = am;
+    put(1, am);
     if (D) D[stride] = dm;
     for (int m = 1; m < L; ++m) {
       dm = rec[4 * m] * dm + (rec[4 * m + 1] * sh2) * am;
       am += dm;
-      A[(m + 1) * stride] = am;
+      put(m + 1, am);
       if (D) D[(m + 1) * stride] = dm;
     }
-    if (dw_out)
-      for (int m = 0; m <= L; ++m) reinterpret_cast<float2*>(A)[m * stride] = dw_from(A[m * stride]);
     return;
   }
-  // Miller: backward from N with A~_{N+1} = 0, A~_N = 1; rescale on growth; normalise by A_0.
+  // Miller: backward from N with B_{N+1} = 0, B_N = 1 (A~_m = w_m B_m); rescale on growth; normalise
+  // by A_0.
   int N = L + (int)ceil(kMillerLog / (2 * b)) + 16;
   if (N > rec_len - 2) N = rec_len - 2;
   const double ch = cosh(b);
-  double up = 0.0, cur = 1.0;   // A~_{m+1}, A~_m
+  double up = 0.0, cur = 1.0;   // B_{m+1}, B_m
   for (int m = N; m >= 1; --m) {
-    const double prev = rec[4 * m + 2] * ch * cur - rec[4 * m + 3] * up;   // A~_{m-1}
+    const double prev = fma(rec[4 * m + 2] * ch, cur, -up);   // B_{m-1}
     up = cur;
     cur = prev;
     if (m - 1 <= L) A[(m - 1) * stride] = cur;
-    // |A~| grows by at most 4 cosh(b) <= 4 cosh 4 per step: checking every 8 steps keeps it below 1e215
+    // |B| grows by at most (4 cosh(b) + 1) a step over two steps (t_m alternates about 4/5 and 4):
+    // checking every 8 steps keeps it below 1e220
     if ((m & 7) == 0 && fabs(cur) > 1e200) {
       cur *= 1e-200;
       up *= 1e-200;
       for (int j = m - 1; j <= L; ++j) A[j * stride] *= 1e-200;
     }
   }
-  const double f = A0 / A[0];
+  const double f = A0 / A[0];   // w_0 = 1
+  if (dw_out) {   // normalised and split into double words in one pass
+    for (int m = 0; m <= L; ++m) reinterpret_cast<float2*>(A)[m * stride] = dw_from(A[m * stride] * (rec[4 * m + 3] * f));
+    return;
+  }
   double prevA = 0.0;
   for (int m = 0; m <= L; ++m) {
-    const double am = A[m * stride] * f;
+    const double am = A[m * stride] * (rec[4 * m + 3] * f);
     A[m * stride] = am;
     if (D && m) D[m * stride] = am - prevA;
     prevA = am;
   }
   if (D) D[0] = A[0] - A[stride];
-  if (dw_out)
-    for (int m = 0; m <= L; ++m) reinterpret_cast<float2*>(A)[m * stride] = dw_from(A[m * stride]);
 }
 
 // ------------------------------------------------------------------ small helpers of phase D
@@ -492,6 +498,15 @@ __device__ __forceinline__ void phase_d_single(const PairArgs& a, const Smem& sm
   for (int pi = 0; pi < nb; ++pi) {
     const PairInfo pr = bcast(mine, pi);
     const int64_t p = a.out_mod ? (a.out_base + p0 + pi) % a.out_mod : p0 + pi;   // output slot
+    // the next pair's records (rho^2 on the ring, e^{ila}) on their way to L2 while this pair runs:
+    // one 128-byte line per lane, every line starting inside its record
+    if (pi + 1 < nb) {
+      const char* nr = reinterpret_cast<const char*>(R2 + (pi + 1) * Mt);
+      const char* ne = reinterpret_cast<const char*>(E + (pi + 1) * 33);
+      const int lr = (Mt * 8 + 127) / 128, le = (33 * 16 + 127) / 128;
+      const char* pf = lane < lr ? nr + lane * 128 : (lane < lr + le ? ne + (lane - lr) * 128 : nullptr);
+      if (pf && __isGlobal(pf)) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+    }
     if (!pr.valid) {
       if (a.modes_out)
         for (int m = lane; m < 2 * (Mt + 1); m += 32) a.modes_out[p * 2 * (Mt + 1) + m] = 0.0;
@@ -1370,14 +1385,20 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
 }
 
 // ------------------------------------------------------------------ host side
+// Columns 2, 3 serve Miller's recurrence A~_{m-1} = c_m cosh(b) A~_m - d_m A~_{m+1}, c_m = 4m/(2m-1),
+// d_m = (2m+1)/(2m-1), rescaled as A~_m = w_m B_m with w_{m+1} = w_{m-1} / d_m (w_0 = w_1 = 1) so that
+// B_{m-1} = t_m cosh(b) B_m - B_{m+1}, t_m = c_m w_m / w_{m-1}: one multiply and one FMA a step.
 static std::vector<double> recurrence_table(int n) {
   std::vector<double> r(4 * (size_t)n, 0.0);
+  std::vector<long double> w(n + 1, 1.0L);
+  for (int m = 1; m < n; ++m) w[m + 1] = w[m - 1] * (2.0L * m - 1) / (2.0L * m + 1);
+  r[3] = 1.0;
   for (int m = 1; m < n; ++m) {
     const long double mm = m;
     r[4 * m + 0] = (double)((2 * mm - 1) / (2 * mm + 1));
     r[4 * m + 1] = (double)((8 * mm) / (2 * mm + 1));
-    r[4 * m + 2] = (double)((4 * mm) / (2 * mm - 1));
-    r[4 * m + 3] = (double)((2 * mm + 1) / (2 * mm - 1));
+    r[4 * m + 2] = (double)((4 * mm) / (2 * mm - 1) * w[m] / w[m - 1]);
+    r[4 * m + 3] = (double)w[m];
   }
   return r;
 }
