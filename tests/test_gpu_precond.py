@@ -191,3 +191,35 @@ def test_learned_solve_falls_back_to_the_block_preconditioner(bie, sphere):
                      precond=bie.PRECOND_LEARNED, block=B, net=net, surface=s, k=c["k"])
     assert r["rel_residual"] <= 1e-8
     assert r["fallback_used"] == 1
+
+
+def test_learned_on_a_held_out_system(bie, ggq):
+    """Train on two systems of a harmonic-star family (first-kind S), then solve a held-out member
+    three ways: plain FGMRES, block-diagonal, learned + block.  The learned form reaches 1e-8 and
+    needs fewer iterations than plain FGMRES; against the block-diagonal form, its yardstick, it
+    does not win (the hard directions of the first-kind S are global, beyond the network's
+    receptive field), and the test records both counts rather than asserting a gain it lacks."""
+    ctx = bie.Context()
+    Np, Mt = 4, 32
+    def system(seed, k):
+        s = bie.Surface(ctx, wl.harmonic_star(seed, 400, 0.12), Np, Mt, ggq)
+        A = bie.assemble(s, bie.OP_S, k)
+        return s, A, bie.BlockDiag(ctx, A, 16 * Mt), k
+    train = [system(1, 5.5), system(2, 7.0)]
+    net = bie.Net(ctx, seed=7)
+    sets = [bie.TrainSet(ctx, s, k, A, B) for s, A, B, k in train]
+    hist = net.train(sets, steps=300, batch=8, lr=1e-3, seed=4)
+    assert np.mean(hist[-40:]) < np.mean(hist[:10])
+    s, A, B, k = system(3, 6.3)                  # held out
+    g = bie.rhs(s, 0, [0.0, 0.0, 1.0], k)
+    x0, r0 = bie.solve(ctx, A, g, tol=1e-8, restart=200, maxit=3000)
+    x1, r1 = bie.solve(ctx, A, g, tol=1e-8, restart=200, maxit=3000, precond=bie.PRECOND_BLOCK, block=B)
+    x2, r2 = bie.solve(ctx, A, g, tol=1e-8, restart=200, maxit=3000, precond=bie.PRECOND_LEARNED, block=B,
+                       net=net, surface=s, k=k)
+    for r in (r0, r1, r2):
+        assert r["rel_residual"] <= 1e-8
+    assert float(torch.linalg.norm(x2 - x1) / torch.linalg.norm(x1)) < 1e-6
+    assert r2["iterations"] < r0["iterations"], (r2["iterations"], r0["iterations"])
+    print("held-out k = %.1f: plain %d it %.3f s, block %d it %.3f s, learned + block %d it %.3f s (fallback %d)"
+          % (k, r0["iterations"], r0["seconds"], r1["iterations"], r1["seconds"], r2["iterations"], r2["seconds"],
+             r2["fallback_used"]))
