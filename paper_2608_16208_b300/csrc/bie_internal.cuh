@@ -127,9 +127,16 @@ __device__ __forceinline__ void scpow_d(double st, double ct, int p, int q, doub
 struct Geo {
   R3 r, rt, rth, rtt, rtth, rthth;
 };
-static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double th, int order, Geo* g) {
+// tsc: sin t, cos t when the caller holds them (a fixed t over many calls), else null
+static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double th, int order, Geo* g,
+                                              const double2* tsc = nullptr) {
   double st, ct, sp, cp;
-  sincos(t, &st, &ct);
+  if (tsc) {
+    st = tsc->x;
+    ct = tsc->y;
+  } else {
+    sincos(t, &st, &ct);
+  }
   sincos(th, &sp, &cp);
   if (S.kind == 0) {
     g->r = {S.ax * st * cp, S.ay * st * sp, S.az * ct};
@@ -252,9 +259,15 @@ static __device__ __noinline__ void surf_eval(const SurfP& S, double t, double t
 }
 
 // r, r_t, r_th at real t and complex th (analytic continuation in theta).
-static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx th, C3* r, C3* rt, C3* rth) {
+static __device__ __noinline__ void surf_eval_c(const SurfP& S, double t, cplx th, C3* r, C3* rt, C3* rth,
+                                                const double2* tsc = nullptr) {
   double st, ct;
-  sincos(t, &st, &ct);
+  if (tsc) {
+    st = tsc->x;
+    ct = tsc->y;
+  } else {
+    sincos(t, &st, &ct);
+  }
   cplx cp, sp;
   ccossin(th, &cp, &sp);
   if (S.kind == 0) {

@@ -103,10 +103,11 @@ __device__ __forceinline__ PairInfo bcast(const PairInfo& p, int src) {
 }
 
 // tb: the pair's star table (stars with at most kStarTabTerms terms), or null
-__device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, const StarTab* tb, cplx z, cplx* f, cplx* df) {
+__device__ inline void rho2_cplx(const SurfP& S, const PairInfo& P, const StarTab* tb, const double2* tsc, cplx z,
+                                 cplx* f, cplx* df) {
   C3 r, rt, rth;
   if (tb) surf_eval_c_star_tab(S, *tb, z, &r, &rt, &rth);
-  else surf_eval_c(S, P.ts, z, &r, &rt, &rth);
+  else surf_eval_c(S, P.ts, z, &r, &rt, &rth, tsc);
   C3 Y = {r.x - C(P.x), r.y - C(P.y), r.z - C(P.z)};
   const bool near = fabs(P.ts - P.t) + fabs(wrap_pi(z.re - P.th)) <= kStableDelta ||
                     abs2(Y.x) + abs2(Y.y) + abs2(Y.z) <= kStableDist * kStableDist;
@@ -126,10 +127,12 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
     star_tab_fill(S, P.ts, P.t, P.th, &tbs);
     tb = &tbs;
   }
+  double2 tsc;   // sin t_s, cos t_s for every evaluation of the ring
+  sincos(P.ts, &tsc.x, &tsc.y);
   auto eval_r = [&](double z) {
     Geo G;
     if (tb) surf_eval_star_tab(S, *tb, z, 2, &G);
-    else surf_eval(S, P.ts, z, 2, &G);
+    else surf_eval(S, P.ts, z, 2, &G, &tsc);
     const double yx = G.r.x - P.x, yy = G.r.y - P.y, yz = G.r.z - P.z;
     g0 = yx * yx + yy * yy + yz * yz;
     g1 = 2 * (yx * G.rth.x + yy * G.rth.y + yz * G.rth.z);
@@ -155,7 +158,7 @@ __device__ __noinline__ void locate_root(const SurfP& S, int Mt, PairInfo& P) {
   bool done = P.capped, extra = false;
   for (int it = 0; it < 60 && !done; ++it) {
     cplx f, df;
-    rho2_cplx(S, P, tb, z, &f, &df);
+    rho2_cplx(S, P, tb, &tsc, z, &f, &df);
     const cplx dz = cdiv(f, df);
     cplx zn = z - dz;
     if (zn.im < 0) zn = conj(zn);
