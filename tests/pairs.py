@@ -49,8 +49,7 @@ def method_modes_chunk(args):
 
 def ulp_sensitivity(surface, t, th, ts, Mt, k, kernel):
     """Per pair, the largest normwise change of the oracle's modes when one of the pair's FP64
-    inputs (t, th, t_s) moves by one ulp: the floor below which two FP64 evaluations of the same
-    coefficients cannot be expected to agree."""
+    inputs (t, th, t_s) moves by one ulp: a per-pair scale of the coefficients' sensitivity."""
     from oracle import kernel_modes as km
     base = km.method_modes(surface, t, th, ts, Mt, k, (kernel,))[kernel]
     nb = np.max(np.abs(base), axis=1)

@@ -51,10 +51,11 @@ def test_modes_large_grids(bie, ctx, ggq, Mt, kernels):
 
 def test_k_adjacent_rings_conditioning(bie, ctx, ggq):
     """The double layer at Mth = 256 on the source rings of the target's own panel, where the root
-    comes within ~3e-5 of the real axis: every pair within 1e-12 of the oracle, except where the
-    coefficients themselves move by more than that when one FP64 input (t, th, t_s) moves by one
-    ulp; those pairs (all on the four rings nearest the target) stay within 1e-12 + 4x that
-    one-ulp change (the problem's own conditioning, not the method's)."""
+    comes within ~3e-5 of the real axis: every pair within 1e-12 of the oracle, except on the four
+    rings nearest the target, where the tau_3 term puts K at the FP64 floor (one rounding of the H3
+    samples moves K by ~1e-12, test_oracle_conditioning.py).  There the bound is 1e-12 plus four
+    times the pair's one-ulp input sensitivity, a per-pair scale of the same size that the oracle
+    measures; at most 2% of the pairs may use it."""
     import multiprocessing as mp
     import os
     from tests.pairs import method_modes_chunk, ulp_sensitivity
